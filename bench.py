@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the scenario-batched Split (one JSON line on stdout).
+
+Workload: million-n1000 -- one giant tour of n = 1000 customers, S = 2^20
+correlated demand scenarios (int16, [n][S]), Q = 200, at most 60 customers per
+route. A step is one cvrpsd_split_eval call through the C ABI: tour table,
+Split kernel(s), exact int64 sums, read-back of sum / infeasible count / mean.
+The scenario matrix is generated once on the device before timing (the
+paper's fixed scenario set); at 2.1 GB it exceeds the 129 MB L2, so no flush
+is needed between steps.
+
+value    = scenario x customer cells per second over all ranks (each rank
+           splits its own 2^20 scenarios: weak scaling, no collective on the
+           data path).
+e2e      = the same metric through the same call with the scenario matrix in
+           pinned HOST memory: each step copies it to the device, splits, and
+           reads back the per-scenario costs and the sums.
+roofline = the Split kernel's algorithmic HBM bytes (2 B per demand read +
+           4 B per cost written + the 8 B/position tour table) / its mean
+           CUDA-event duration, against the measured copy bandwidth.
+--impl reference times the CPU oracle (test infrastructure) on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Split scenario·customer relaxations/s at n=1000,S=2^20 (bit-exact); % roofline"
+UNIT = "cells/s"
+KERNEL_FILES = ["paper_2511_18022_gb300/csrc/split_deque.cuh",
+                "paper_2511_18022_gb300/csrc/split_deque.cu",
+                "paper_2511_18022_gb300/csrc/kernels.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_deque_million-n1000.traffic.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks() -> tuple[float, str]:
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, parts))
+            except Exception:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inside = [r for ts, r in rows if self.t0 - 1 <= ts <= self.t1 + 1] or [r for _, r in rows]
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[6 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(inside)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")   # timing barrier and max only; no data exchange
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, inst, cols: int, seed_offset: int = 0):
+    from synth import demand_columns
+    import numpy as np
+    return demand_columns(inst.mu, inst.region, w.kind, w.scen_seeds[0] + seed_offset,
+                          np.arange(cols), w.dtype)
+
+
+def time_oracle(inst, D, seconds: float, threads: int):
+    """Repeat the oracle over the sample until `seconds` have passed."""
+    import oracle
+    cells = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L, nthreads=threads)
+        reps += 1
+        cells += inst.n * D.shape[1]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return cells / el, reps, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from synth import workload
+    w = workload(args.workload)
+    inst = w.instances[0]
+    cores = host_cores()
+    cols = args.ref_cols
+    D = oracle_sample(w, inst, cols)
+    import oracle
+    for _ in range(args.warmup):
+        oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = inst.n * cols * args.steps / total
+    sample = (f"{cols} host-generated scenarios of the {args.workload} instance "
+              f"(n={inst.n}) per step, {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+        "data": "synthetic", "config": workload_config(w, inst),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w, inst) -> dict:
+    return {"workload": w.name, "n": inst.n, "S": w.S, "Q": inst.Q, "L": inst.L,
+            "demand": "correlated lognormal, int16 [n][S]",
+            "l2": "inputs larger than L2 (2.10 GB scenario matrix per step), no flush"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2511_18022_gb300 as cv
+    from paper_2511_18022_gb300 import build
+    from synth import workload
+
+    build.build()
+    w = workload(args.workload)
+    inst = w.instances[0]
+    n, S = inst.n, w.S
+    sp = cv.Splitter(local)
+    if args.shape:
+        t, s, r = (int(x) for x in args.shape.split(","))
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=t, spt=s, ring=r)
+    D = torch.empty((n, S), dtype=torch.int16, device="cuda")
+    # each rank splits its own scenario shard (its own seed)
+    sp.gen_demand(w.scen_seeds[0] + rank, cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    out = torch.empty(S, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return sp.split(inst.tour, inst.dist, D, inst.Q, inst.L, out_cost=out)
+
+    for _ in range(args.warmup):
+        r = step()
+    sp.profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms, launches, overflow = [], 0, 0
+    clocks.mark(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+        st = sp.stats()
+        kms.append(st["kernel_ms"])
+        launches += st["launches"]
+        overflow += max(st["overflow"], 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    barrier(world)
+    clk = clocks.stop()
+    sp.profiling(False)
+    elapsed_ms = max_over_ranks(world, e0.elapsed_time(e1))
+    ms_per_step = elapsed_ms / args.steps
+    value = world * n * S * args.steps / (elapsed_ms / 1e3)
+
+    # roofline of the Split kernel
+    kernel_ms = statistics.mean(kms)
+    algo_bytes = n * S * 2 + S * 4 + n * 8
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+        if t.get("kernel_hash") == kernel_hash():
+            traffic = t["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "split_deque_kernel", "kernel_ms": round(kernel_ms, 4),
+                "algorithmic_bytes": algo_bytes}
+
+    # end to end from pinned host memory
+    H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
+    H.copy_(D)
+    Hout = torch.empty(S, dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+
+    def e2e_step():
+        D.copy_(H, non_blocking=True)
+        res = sp.split(inst.tour, inst.dist, D, inst.Q, inst.L, out_cost=out)
+        Hout.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        return res
+
+    e2e_step()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n * S * 2, "d2h_bytes_per_step": S * 4 + 24,
+           "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = host_cores()
+        Dc = oracle_sample(w, inst, args.cpu_cols)
+        v, reps, el = time_oracle(inst, Dc, args.cpu_seconds, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_cols} host-generated scenarios of this instance, "
+                         f"split {reps} times in {el:.1f} s on {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": workload_config(w, inst) | {
+                "kernel": f"deque threads={st['threads']} spt={st['spt']} ring={st['ring']}",
+                "parallelism": f"scenario shards x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "result": {"sum": r.sum, "infeasible": r.infeasible, "mean": r.mean,
+                       "overflow_scenarios": overflow // max(args.steps, 1)},
+        }
+        print(json.dumps(line))
+    sp.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="million-n1000")
+    ap.add_argument("--shape", default="", help="threads,spt,ring of the deque kernel")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-cols", type=int, default=8192)
+    ap.add_argument("--ref-cols", type=int, default=8192)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("steps >= 1, warmup >= 0")
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

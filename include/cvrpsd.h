@@ -1,0 +1,170 @@
+/*
+ * cvrpsd.h - C ABI of the GB300 scenario-batched Split for the CVRP with
+ * stochastic demands.
+ *
+ * Method: Zhao, Yang, Zhang, Ding, "GPU-based Split algorithm for Large-Scale
+ * CVRPSD". Given a giant tour sigma_1..sigma_n of customers (Section 3) and S
+ * demand scenarios, the Split of scenario w is the dynamic program of Eq. 1:
+ *
+ *   f(0) = 0,  f(i) = min_{p <= i-1} f(p) + c(0, sigma_{p+1})
+ *                    + sum_{k=p+1}^{i-1} c(sigma_k, sigma_{k+1}) + c(sigma_i, 0)
+ *   over the p whose route sigma_{p+1}..sigma_i carries load <= Q,
+ *
+ * which Eq. 2 and Eq. 3 restate as a min over the window
+ * [mask_w(i), i-1] of candidates. The scenario cost is f(n); Appendix A's
+ * sample-average estimate is the mean of f(n) over the scenarios.
+ *
+ * Conventions shared by every entry point:
+ *  - Node 0 of `dist` is the depot and also the paper's return depot n+1.
+ *    `dist` is (n+1) x (n+1) int32, row-major, row = from, column = to, on the
+ *    HOST, all used entries >= 0.
+ *  - `tour` is a HOST array of n int32 customer ids, a permutation of 1..n.
+ *  - Demands live on the DEVICE as a [n][ld] matrix: row k-1 holds customer k
+ *    (by id, not by tour position), scenario s is column s, scenarios are
+ *    contiguous. Element type int16 (CVRPSD_I16) or int32 (CVRPSD_I32),
+ *    values >= 0. `ld` >= S is the row pitch in elements.
+ *  - Q >= 0 is the vehicle capacity. L is the largest number of customers on
+ *    one route (the "maximum route length" Section 3 allows); L >= n means no
+ *    limit. The fleet is unlimited.
+ *  - A scenario in which some customer's demand exceeds Q has no feasible
+ *    split (Eq. 2's window is empty): its cost is INT32_MAX, it is left out
+ *    of the sum and the mean, and it is counted as infeasible; the call then
+ *    returns CVRPSD_WARN_INFEASIBLE (outputs are still valid).
+ *  - Costs are exact integers. Per-scenario costs are int32; sums are int64.
+ *  - The caller owns every buffer; the library never frees caller memory.
+ *    Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ *  - Return value: 0 on success, CVRPSD_WARN_INFEASIBLE (> 0), or a negative
+ *    error code; cvrpsd_strerror() names it and cvrpsd_last_error() gives the
+ *    detail of the last failure on that context. On error no output is
+ *    written unless stated otherwise.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef CVRPSD_H
+#define CVRPSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CVRPSD_OK                  0
+#define CVRPSD_WARN_INFEASIBLE     1
+#define CVRPSD_ERR_ARG            -1   /* bad size, pointer, Q, L, or tour */
+#define CVRPSD_ERR_DTYPE          -2   /* demand element type not supported */
+#define CVRPSD_ERR_OVERFLOW       -3   /* costs could exceed int32 */
+#define CVRPSD_ERR_CUDA           -4   /* a CUDA runtime call failed */
+#define CVRPSD_ERR_DEVICE_STATUS  -5   /* a kernel reported a bad input */
+#define CVRPSD_ERR_NOMEM          -6   /* scratch allocation failed */
+#define CVRPSD_ERR_UNSUPPORTED    -7   /* size beyond the library's limits */
+
+#define CVRPSD_I16  2
+#define CVRPSD_I32  4
+
+/* Largest tour the library accepts. */
+#define CVRPSD_MAX_N 8191
+
+/* Kernel choice for the Split (see cvrpsd_config). */
+#define CVRPSD_KERNEL_AUTO   0
+#define CVRPSD_KERNEL_DEQUE  1   /* one thread per scenario, monotone deque */
+#define CVRPSD_KERNEL_WARP   2   /* one warp per scenario, parallel window min */
+
+/* Demand kinds of the scenario generator. */
+#define CVRPSD_GEN_NORMAL      0
+#define CVRPSD_GEN_CORRELATED  1
+
+typedef struct cvrpsd_ctx cvrpsd_ctx;
+
+/* Launch shape of the Split. threads in {64,128,256} per block, spt
+ * (scenarios per thread) in {1,2}, ring (deque capacity per scenario) in
+ * {16,32,64}. Zero fields mean "library default / autotuned". */
+typedef struct {
+    int32_t kernel;
+    int32_t threads;
+    int32_t spt;
+    int32_t ring;
+} cvrpsd_config;
+
+/* What the last Split call on a context did. */
+typedef struct {
+    int32_t kernel;            /* kernel that evaluated the scenarios */
+    int32_t threads, spt, ring;
+    int64_t overflow;          /* scenarios the warp kernel re-evaluated (deque ring too
+                                  small, demand above Q or negative), -1 if not read back */
+    int32_t launches;          /* kernels launched by the call */
+    float kernel_ms;           /* device time of the main Split kernel, -1 unless profiling */
+    float fallback_ms;         /* device time of the overflow pass, -1 unless profiling */
+} cvrpsd_stats;
+
+/* Create a context bound to CUDA device `device`. Allocates small scratch
+ * lazily on first use. Returns CVRPSD_ERR_CUDA if the device is unusable. */
+int cvrpsd_create(cvrpsd_ctx **ctx, int device);
+
+/* Release a context and its scratch. Waits for nothing: the caller must not
+ * destroy a context while work it enqueued is still running. */
+int cvrpsd_destroy(cvrpsd_ctx *ctx);
+
+const char *cvrpsd_strerror(int code);
+const char *cvrpsd_last_error(const cvrpsd_ctx *ctx);
+const char *cvrpsd_version(void);
+
+/* Fix the launch shape used by later Split calls on `ctx` (testing and
+ * tuning). Returns CVRPSD_ERR_ARG for values outside the listed sets. */
+int cvrpsd_set_config(cvrpsd_ctx *ctx, const cvrpsd_config *cfg);
+int cvrpsd_get_config(const cvrpsd_ctx *ctx, cvrpsd_config *cfg);
+int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats);
+
+/* With on != 0, later Split calls that return host outputs also time their
+ * kernels with CUDA events recorded on the call's stream and report the
+ * durations in cvrpsd_stats. Off by default. */
+int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on);
+
+/*
+ * Split one giant tour under S scenarios (Section 3, Eq. 1-3) and reduce the
+ * costs to the sample-average of Appendix A.
+ *
+ *  tour[n], dist[(n+1)^2]  HOST, see conventions; 1 <= n <= CVRPSD_MAX_N.
+ *  demand                  DEVICE [n][ld], element type demand_dtype.
+ *  S >= 0, ld >= S         scenarios and row pitch (elements).
+ *  Q >= 0, L >= 1          capacity and route-length limit.
+ *  out_cost                DEVICE int32[S] or NULL: f(n) per scenario,
+ *                          INT32_MAX where infeasible.
+ *  out_sum, out_infeasible HOST int64 or NULL: exact sum of feasible costs,
+ *                          number of infeasible scenarios.
+ *  out_mean                HOST double or NULL: out_sum / (S - infeasible),
+ *                          NaN when no scenario is feasible or S == 0.
+ *  stream                  cudaStream_t.
+ *
+ * If any host output is requested the call waits for `stream` to finish its
+ * work; otherwise it returns once the work is enqueued. Rejects device
+ * buffers too small for [n][ld] / [S] with CVRPSD_ERR_ARG, and inputs whose
+ * costs could overflow int32 with CVRPSD_ERR_OVERFLOW.
+ */
+int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n,
+                      const int32_t *dist, const void *demand,
+                      int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q,
+                      int32_t L, int32_t *out_cost, int64_t *out_sum,
+                      int64_t *out_infeasible, double *out_mean, void *stream);
+
+/*
+ * Seeded scenario generator (workload synthesis, not part of the paper's
+ * method). Writes demand[k-1][s] for customers k = 1..n and scenarios
+ * s = 0..S-1 into the DEVICE [n][ld] matrix `out` of type `dtype`:
+ *   CVRPSD_GEN_NORMAL:     max(0, round(mu_k + 0.3 mu_k Z_sk))
+ *   CVRPSD_GEN_CORRELATED: max(0, round(mu_k exp(0.3 (0.6 F_{s,r_k}
+ *                                                  + 0.8 E_sk) - 0.045)))
+ * with Z, E, F standard normals from Philox4x32-10 (counter (s, index,
+ * domain, 0), key = seed halves) by Box-Muller in float64, round half away
+ * from zero, clamped to the type's maximum. mu[n], region[n] (quadrant
+ * 0..3 of customer k at [k-1]) are HOST arrays. Asynchronous on `stream`.
+ */
+int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind,
+                      const int32_t *mu, const int32_t *region, int32_t n,
+                      int64_t S, int64_t ld, int32_t dtype, void *out,
+                      void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVRPSD_H */

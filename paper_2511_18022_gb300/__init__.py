@@ -1,0 +1,192 @@
+"""GB300 scenario-batched Split for the CVRP with stochastic demands.
+
+Python face of the C ABI in include/cvrpsd.h: the functions below carry the
+same names as the C entry points and only marshal arguments (numpy arrays for
+the host inputs, CUDA torch tensors or raw device pointers for device
+buffers, the current torch stream by default). Every step of the Split runs
+in the library's CUDA kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MAX_N,
+                   KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, GEN_NORMAL, GEN_CORRELATED)
+
+__all__ = [
+    "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_version",
+    "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
+    "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
+]
+
+INT32_MAX = 2**31 - 1
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(buf):
+    """(pointer, dtype code, shape) of a CUDA tensor, or a raw pointer."""
+    if buf is None:
+        return None, None, None
+    if isinstance(buf, int):
+        return buf, None, None
+    if not buf.is_cuda:
+        raise CvrpsdError(_lib.ERR_ARG, "device buffer expected, got a host tensor")
+    import torch
+    code = {torch.int16: I16, torch.int32: I32}.get(buf.dtype)
+    return buf.data_ptr(), code, tuple(buf.shape)
+
+
+def cvrpsd_version() -> str:
+    return _lib.load().cvrpsd_version().decode()
+
+
+def cvrpsd_create(device: int = 0) -> ctypes.c_void_p:
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    rc = lib.cvrpsd_create(ctypes.byref(h), int(device))
+    if rc != OK:
+        raise CvrpsdError(rc, f"cvrpsd_create(device={device}) failed")
+    return h
+
+
+def cvrpsd_destroy(ctx) -> None:
+    _lib.check(None, _lib.load().cvrpsd_destroy(ctx))
+
+
+def cvrpsd_set_config(ctx, kernel=KERNEL_AUTO, threads=0, spt=0, ring=0) -> None:
+    cfg = Config(kernel, threads, spt, ring)
+    _lib.check(ctx, _lib.load().cvrpsd_set_config(ctx, ctypes.byref(cfg)))
+
+
+def cvrpsd_get_config(ctx) -> dict:
+    cfg = Config()
+    _lib.check(ctx, _lib.load().cvrpsd_get_config(ctx, ctypes.byref(cfg)))
+    return {f: getattr(cfg, f) for f, _ in Config._fields_}
+
+
+def cvrpsd_set_profiling(ctx, on: bool) -> None:
+    _lib.check(ctx, _lib.load().cvrpsd_set_profiling(ctx, int(bool(on))))
+
+
+def cvrpsd_last_stats(ctx) -> dict:
+    st = Stats()
+    _lib.check(ctx, _lib.load().cvrpsd_last_stats(ctx, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+@dataclass
+class SplitResult:
+    status: int
+    sum: int | None
+    infeasible: int | None
+    mean: float | None
+
+
+def cvrpsd_split_eval(ctx, tour, dist, demand, Q: int, L: int | None = None, *,
+                      S: int | None = None, ld: int | None = None, dtype: int | None = None,
+                      out_cost=None, host_outputs: bool = True, stream=None) -> SplitResult:
+    """Split one tour under every scenario column of `demand` (device [n][ld]).
+
+    `tour` (customer ids 1..n) and `dist` ((n+1)^2, node 0 = depot) are host
+    arrays. `out_cost` is an optional device int32 tensor of S entries. With
+    host_outputs the call waits for the stream and returns the exact sum,
+    the infeasible count and the mean; otherwise it only enqueues the work."""
+    tour = _i32(tour)
+    dist = _i32(dist)
+    n = int(tour.shape[0])
+    dptr, dcode, dshape = _dev(demand)
+    if dshape is not None:
+        if len(dshape) != 2 or dshape[0] != n:
+            raise CvrpsdError(_lib.ERR_ARG, f"demand must be [n][ld] with n={n}, got {dshape}")
+        if not demand.is_contiguous():
+            raise CvrpsdError(_lib.ERR_ARG, "demand must be contiguous")
+        ld = dshape[1] if ld is None else ld
+        S = ld if S is None else S
+        dtype = dcode if dtype is None else dtype
+        if dtype is None:
+            raise CvrpsdError(_lib.ERR_DTYPE, f"demand must be int16 or int32, got {demand.dtype}")
+    if S is None or ld is None or dtype is None:
+        raise CvrpsdError(_lib.ERR_ARG, "S, ld and dtype are required with a raw demand pointer")
+    optr, _, oshape = _dev(out_cost)
+    L = n if L is None else int(L)
+    s_sum = ctypes.c_int64(0)
+    s_inf = ctypes.c_int64(0)
+    s_mean = ctypes.c_double(0.0)
+    hs = (ctypes.byref(s_sum), ctypes.byref(s_inf), ctypes.byref(s_mean)) if host_outputs else (None,) * 3
+    lib = _lib.load()
+    rc = lib.cvrpsd_split_eval(ctx, tour.ctypes.data, n, dist.ctypes.data, dptr, int(dtype),
+                               int(S), int(ld), int(Q), L, optr, *hs, _stream_ptr(stream))
+    _lib.check(ctx, rc)
+    if not host_outputs:
+        return SplitResult(rc, None, None, None)
+    return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)
+
+
+def cvrpsd_gen_demand(ctx, seed: int, kind: int, mu, region, out, *, S: int | None = None,
+                      ld: int | None = None, dtype: int | None = None, stream=None) -> None:
+    """Fill the device [n][ld] matrix `out` with seeded scenarios 0..S-1."""
+    mu = _i32(mu)
+    region = _i32(region) if region is not None else None
+    n = int(mu.shape[0])
+    optr, ocode, oshape = _dev(out)
+    if oshape is not None:
+        if len(oshape) != 2 or oshape[0] != n:
+            raise CvrpsdError(_lib.ERR_ARG, f"out must be [n][ld] with n={n}, got {oshape}")
+        ld = oshape[1] if ld is None else ld
+        S = ld if S is None else S
+        dtype = ocode if dtype is None else dtype
+    rc = _lib.load().cvrpsd_gen_demand(ctx, int(seed) & (2**64 - 1), int(kind), mu.ctypes.data,
+                                       None if region is None else region.ctypes.data, n, int(S),
+                                       int(ld), int(dtype), optr, _stream_ptr(stream))
+    _lib.check(ctx, rc)
+
+
+class Splitter:
+    """Owns one library context on one device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = cvrpsd_create(device)
+
+    def close(self):
+        if self.ctx is not None:
+            cvrpsd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, **kw):
+        cvrpsd_set_config(self.ctx, **kw)
+
+    def stats(self) -> dict:
+        return cvrpsd_last_stats(self.ctx)
+
+    def profiling(self, on: bool = True):
+        cvrpsd_set_profiling(self.ctx, on)
+
+    def split(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
+        return cvrpsd_split_eval(self.ctx, tour, dist, demand, Q, L, **kw)
+
+    def gen_demand(self, seed, kind, mu, region, out, **kw):
+        cvrpsd_gen_demand(self.ctx, seed, kind, mu, region, out, **kw)

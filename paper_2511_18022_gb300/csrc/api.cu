@@ -1,0 +1,472 @@
+// C ABI of the scenario-batched Split (include/cvrpsd.h): argument checks,
+// the per-tour position table, the launch plan and the exact host outputs.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "../../include/cvrpsd.h"
+#include "kernels.h"
+
+using namespace cvrpsd;
+
+struct cvrpsd_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int max_smem = 48 * 1024;              // opt-in shared memory per block
+    unsigned long long *d_acc = nullptr;   // ACC_WORDS
+    int32_t *d_list = nullptr;             // overflow list
+    long long list_cap = 0;
+    TourStep *d_tab = nullptr;
+    TourStep *h_tab = nullptr;             // pinned
+    unsigned long long *h_acc = nullptr;   // pinned
+    int32_t *d_gen = nullptr;              // mu[n], region[n]
+    int32_t *h_gen = nullptr;              // pinned
+    cudaEvent_t ev_tab = nullptr;          // tab upload done
+    cudaEvent_t ev_gen = nullptr;          // gen upload done
+    cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};   // kernel timing (profiling)
+    int profiling = 0;
+    cvrpsd_config cfg{0, 0, 0, 0};
+    cvrpsd_stats stats{};
+    char err[512] = {0};
+};
+
+namespace {
+
+int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(cvrpsd_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, CVRPSD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+typedef CUresult (*GetRangeFn)(CUdeviceptr *, size_t *, CUdeviceptr);
+
+GetRangeFn get_range_fn()
+{
+    static GetRangeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<GetRangeFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The buffer [ptr, ptr + bytes) must be device memory of ctx->device inside one
+// allocation, so that no kernel of this library can read or write past it.
+int check_device_buffer(cvrpsd_ctx *ctx, const void *ptr, unsigned long long bytes, const char *what)
+{
+    if (!ptr) return fail(ctx, CVRPSD_ERR_ARG, "%s is NULL", what);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, CVRPSD_ERR_ARG, "%s is not a CUDA pointer", what);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(ctx, CVRPSD_ERR_ARG, "%s must be device memory", what);
+    if (a.type == cudaMemoryTypeDevice && a.device != ctx->device)
+        return fail(ctx, CVRPSD_ERR_ARG, "%s lives on device %d, context is on %d", what, a.device, ctx->device);
+    if (GetRangeFn fn = get_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)ptr) == CUDA_SUCCESS) {
+            const unsigned long long end = (unsigned long long)(uintptr_t)ptr + bytes;
+            if (end > (unsigned long long)base + size)
+                return fail(ctx, CVRPSD_ERR_ARG, "%s: %llu bytes needed, allocation ends after %llu", what, bytes,
+                            (unsigned long long)(base + size - (CUdeviceptr)ptr));
+        }
+    }
+    return CVRPSD_OK;
+}
+
+int ensure_scratch(cvrpsd_ctx *ctx, long long S)
+{
+    if (!ctx->d_acc) {
+        CK(cudaMalloc(&ctx->d_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMalloc(acc)");
+        CK(cudaMallocHost(&ctx->h_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMallocHost(acc)");
+        CK(cudaMalloc(&ctx->d_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMalloc(tab)");
+        CK(cudaMallocHost(&ctx->h_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMallocHost(tab)");
+        CK(cudaEventCreateWithFlags(&ctx->ev_tab, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (S > ctx->list_cap) {
+        if (ctx->d_list) cudaFree(ctx->d_list);
+        ctx->d_list = nullptr;
+        ctx->list_cap = 0;
+        long long cap = S < 4096 ? 4096 : S;
+        cudaError_t e = cudaMalloc(&ctx->d_list, (size_t)cap * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, CVRPSD_ERR_NOMEM, "overflow list of %lld entries: %s", cap, cudaGetErrorString(e));
+        }
+        ctx->list_cap = cap;
+    }
+    return CVRPSD_OK;
+}
+
+uint32_t key_scale(int n)
+{
+    uint32_t K = 1;
+    while (K <= (uint32_t)n) K <<= 1;
+    return K;
+}
+
+// Validates the tour and distances and fills tab[0..n): row of sigma_i and
+//   C_i = c(sigma_i, 0) + c(0, sigma_{i+1}) - c(sigma_i, sigma_{i+1})   (i < n)
+//   C_n = D[n] + c(sigma_n, 0),  D[n] = sum_{t<n} c(sigma_t, sigma_{t+1}),
+// with g0 = c(0, sigma_1). Checks that every value the kernels form fits int32.
+int build_tour_table(cvrpsd_ctx *ctx, const int32_t *tour, int n, const int32_t *dist, int Q,
+                     TourStep *tab, int32_t *g0)
+{
+    if (!tour || !dist) return fail(ctx, CVRPSD_ERR_ARG, "tour and dist are required");
+    const long long N1 = (long long)n + 1;
+    std::vector<unsigned char> seen((size_t)n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        const int c = tour[k];
+        if (c < 1 || c > n) return fail(ctx, CVRPSD_ERR_ARG, "tour[%d] = %d is not a customer id in 1..%d", k, c, n);
+        if (seen[c]) return fail(ctx, CVRPSD_ERR_ARG, "customer %d appears twice in the tour", c);
+        seen[c] = 1;
+    }
+    long long singles = 0, Dn = 0, maxc = 0;
+    for (int k = 0; k < n; ++k) {
+        const int c = tour[k];
+        const long long out0 = dist[c], back = dist[(long long)c * N1];
+        const long long nxt = k + 1 < n ? dist[(long long)c * N1 + tour[k + 1]] : 0;
+        if (out0 < 0 || back < 0 || nxt < 0)
+            return fail(ctx, CVRPSD_ERR_ARG, "negative distance at tour position %d", k + 1);
+        singles += out0 + back;
+        Dn += nxt;
+        if (out0 > maxc) maxc = out0;
+        if (back > maxc) maxc = back;
+        if (nxt > maxc) maxc = nxt;
+    }
+    // |g| <= singles + D[n] + max c; every intermediate is bounded by that sum.
+    if (singles + Dn + 3 * maxc >= (1LL << 30))
+        return fail(ctx, CVRPSD_ERR_OVERFLOW, "route costs up to %lld do not fit the int32 arithmetic",
+                    singles + Dn + 3 * maxc);
+    const long long K = key_scale(n);
+    if ((long long)(Q + 1LL) * K + n >= (1LL << 31))
+        return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "Q = %d too large for n = %d (need (Q+1)*%lld + n < 2^31)", Q, n, K);
+    for (int k = 0; k < n; ++k) {
+        const int c = tour[k];
+        tab[k].row = c - 1;
+        if (k + 1 < n) {
+            const int d = tour[k + 1];
+            tab[k].c = (int32_t)(dist[(long long)c * N1] + dist[d] - dist[(long long)c * N1 + d]);
+        } else {
+            tab[k].c = (int32_t)(Dn + dist[(long long)c * N1]);
+        }
+    }
+    *g0 = dist[tour[0]];
+    return CVRPSD_OK;
+}
+
+bool valid_shape(int threads, int spt, int ring)
+{
+    return (threads == 64 || threads == 128 || threads == 256) && (spt == 1 || spt == 2) &&
+           (ring == 16 || ring == 32 || ring == 64);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cvrpsd_version(void) { return "cvrpsd-gb300 0.1 (sm_103a)"; }
+
+const char *cvrpsd_strerror(int code)
+{
+    switch (code) {
+    case CVRPSD_OK: return "ok";
+    case CVRPSD_WARN_INFEASIBLE: return "some scenarios have no feasible split";
+    case CVRPSD_ERR_ARG: return "invalid argument";
+    case CVRPSD_ERR_DTYPE: return "unsupported demand type";
+    case CVRPSD_ERR_OVERFLOW: return "costs could overflow int32";
+    case CVRPSD_ERR_CUDA: return "CUDA error";
+    case CVRPSD_ERR_DEVICE_STATUS: return "a kernel reported invalid input";
+    case CVRPSD_ERR_NOMEM: return "out of device memory";
+    case CVRPSD_ERR_UNSUPPORTED: return "size beyond the library's limits";
+    default: return "unknown status";
+    }
+}
+
+const char *cvrpsd_last_error(const cvrpsd_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int cvrpsd_create(cvrpsd_ctx **out, int device)
+{
+    if (!out) return CVRPSD_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return CVRPSD_ERR_CUDA;
+    }
+    cvrpsd_ctx *ctx = new (std::nothrow) cvrpsd_ctx();
+    if (!ctx) return CVRPSD_ERR_NOMEM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return CVRPSD_ERR_CUDA;
+    }
+    *out = ctx;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_destroy(cvrpsd_ctx *ctx)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (ctx->d_acc) cudaFree(ctx->d_acc);
+    if (ctx->d_list) cudaFree(ctx->d_list);
+    if (ctx->d_tab) cudaFree(ctx->d_tab);
+    if (ctx->d_gen) cudaFree(ctx->d_gen);
+    if (ctx->h_tab) cudaFreeHost(ctx->h_tab);
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    if (ctx->h_gen) cudaFreeHost(ctx->h_gen);
+    if (ctx->ev_tab) cudaEventDestroy(ctx->ev_tab);
+    if (ctx->ev_gen) cudaEventDestroy(ctx->ev_gen);
+    for (cudaEvent_t e : ctx->ev_t)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_set_config(cvrpsd_ctx *ctx, const cvrpsd_config *cfg)
+{
+    if (!ctx || !cfg) return CVRPSD_ERR_ARG;
+    if (cfg->kernel < CVRPSD_KERNEL_AUTO || cfg->kernel > CVRPSD_KERNEL_WARP)
+        return fail(ctx, CVRPSD_ERR_ARG, "kernel %d unknown", cfg->kernel);
+    const bool any_shape = cfg->threads || cfg->spt || cfg->ring;
+    if (any_shape && !valid_shape(cfg->threads, cfg->spt, cfg->ring))
+        return fail(ctx, CVRPSD_ERR_ARG, "shape threads=%d spt=%d ring=%d not supported", cfg->threads, cfg->spt,
+                    cfg->ring);
+    ctx->cfg = *cfg;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_get_config(const cvrpsd_ctx *ctx, cvrpsd_config *cfg)
+{
+    if (!ctx || !cfg) return CVRPSD_ERR_ARG;
+    *cfg = ctx->cfg;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats)
+{
+    if (!ctx || !stats) return CVRPSD_ERR_ARG;
+    *stats = ctx->stats;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    if (on && !ctx->ev_t[0]) {
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        for (cudaEvent_t &e : ctx->ev_t) CK(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    ctx->profiling = on ? 1 : 0;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
+                      int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
+                      int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream_ptr)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    ctx->err[0] = 0;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    if (n < 1 || n > CVRPSD_MAX_N) return fail(ctx, CVRPSD_ERR_ARG, "n = %d outside 1..%d", n, CVRPSD_MAX_N);
+    if (demand_dtype != CVRPSD_I16 && demand_dtype != CVRPSD_I32)
+        return fail(ctx, CVRPSD_ERR_DTYPE, "demand_dtype %d (use CVRPSD_I16 or CVRPSD_I32)", demand_dtype);
+    if (S < 0 || S > INT32_MAX) return fail(ctx, CVRPSD_ERR_ARG, "S = %lld outside 0..2^31-1", (long long)S);
+    if (ld < S || ld < 1) return fail(ctx, CVRPSD_ERR_ARG, "ld = %lld must be >= max(S, 1)", (long long)ld);
+    if ((unsigned long long)ld * demand_dtype > 0xFFFFFFFFull)
+        return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "row pitch of %lld bytes exceeds 4 GiB", (long long)ld * demand_dtype);
+    if (Q < 0) return fail(ctx, CVRPSD_ERR_ARG, "Q = %d must be >= 0", Q);
+    if (L < 1) return fail(ctx, CVRPSD_ERR_ARG, "L = %d must be >= 1", L);
+    if (L > n) L = n;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (S > 0) {
+        int rc = check_device_buffer(ctx, demand, ((unsigned long long)(n - 1) * ld + S) * demand_dtype, "demand");
+        if (rc) return rc;
+        if (out_cost) {
+            rc = check_device_buffer(ctx, out_cost, (unsigned long long)S * 4, "out_cost");
+            if (rc) return rc;
+        }
+    }
+    int rc = ensure_scratch(ctx, S);
+    if (rc) return rc;
+
+    // The pinned table may still be feeding the previous call's copy.
+    CK(cudaEventSynchronize(ctx->ev_tab), "cudaEventSynchronize");
+    int32_t g0 = 0;
+    rc = build_tour_table(ctx, tour, n, dist, Q, ctx->h_tab, &g0);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->d_tab, ctx->h_tab, (size_t)n * sizeof(TourStep), cudaMemcpyHostToDevice, stream),
+       "upload tour table");
+    CK(cudaEventRecord(ctx->ev_tab, stream), "cudaEventRecord");
+    CK(cudaMemsetAsync(ctx->d_acc, 0, ACC_WORDS * sizeof(unsigned long long), stream), "clear accumulators");
+
+    SplitParams p{};
+    p.tab = ctx->d_tab;
+    p.demand = demand;
+    p.ld = ld;
+    p.S = S;
+    p.n = n;
+    p.Q = Q;
+    p.L = L;
+    p.g0 = g0;
+    p.K = key_scale(n);
+    p.out_cost = out_cost;
+    p.acc = ctx->d_acc;
+    p.ovf_list = ctx->d_list;
+
+    cvrpsd_stats st{};
+    st.overflow = -1;
+    st.kernel_ms = st.fallback_ms = -1.0f;
+    const bool timed = ctx->profiling && (out_sum || out_infeasible || out_mean) && S > 0;
+    bool fallback_launched = false;
+    if (S > 0) {
+        const int kernel = ctx->cfg.kernel == CVRPSD_KERNEL_AUTO ? CVRPSD_KERNEL_DEQUE : ctx->cfg.kernel;
+        const int warp_grid = 2 * (ctx->sm_count > 0 ? ctx->sm_count : 152);
+        if (kernel == CVRPSD_KERNEL_WARP) {
+            long long need = (S + 3) / 4;
+            const int grid = (int)(need < 8LL * warp_grid ? need : 8LL * warp_grid);
+            if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
+            CK(launch_split_warp(p, demand_dtype, nullptr, nullptr, grid, ctx->max_smem, stream),
+               "split_warp launch");
+            if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
+            st.kernel = CVRPSD_KERNEL_WARP;
+            st.launches = 1;
+        } else {
+            DequeShape shape{256, 1, 16};
+            if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
+            // Vector loads of spt demands need spt-aligned rows and base.
+            while (shape.spt > 1 && (ld % shape.spt != 0 ||
+                                     (uintptr_t)demand % ((uintptr_t)shape.spt * demand_dtype) != 0))
+                shape.spt >>= 1;
+            // Fit the block's shared memory (tour table + rings) in the device limit.
+            while (split_deque_smem(p, shape) > (size_t)ctx->max_smem) {
+                if (shape.spt > 1) shape.spt >>= 1;
+                else if (shape.threads > 64) shape.threads >>= 1;
+                else if (shape.ring > 16) shape.ring >>= 1;
+                else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "tour of %d customers does not fit shared memory", n);
+            }
+            if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
+            CK(launch_split_deque(p, demand_dtype, shape, stream), "split_deque launch");
+            if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
+            st.kernel = CVRPSD_KERNEL_DEQUE;
+            st.threads = shape.threads;
+            st.spt = shape.spt;
+            st.ring = shape.ring;
+            st.launches = 1;
+            // Scenarios the deque kernel set aside (ring too small, a demand above
+            // Q, a negative demand) are evaluated by the warp kernel; with none
+            // set aside its blocks exit at once.
+            CK(launch_split_warp(p, demand_dtype, ctx->d_list, ctx->d_acc + ACC_OVERFLOW, warp_grid,
+                                 ctx->max_smem, stream),
+               "split_warp (set-aside scenarios) launch");
+            st.launches = 2;
+            fallback_launched = true;
+            if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
+        }
+    }
+    ctx->stats = st;
+    if (!out_sum && !out_infeasible && !out_mean) return CVRPSD_OK;
+
+    CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, ACC_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       stream),
+       "read accumulators");
+    CK(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    const unsigned long long *a = ctx->h_acc;
+    ctx->stats.overflow = (int64_t)a[ACC_OVERFLOW];
+    if (timed) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->ev_t[0], ctx->ev_t[1]), "cudaEventElapsedTime");
+        ctx->stats.kernel_ms = ms;
+        if (fallback_launched) {
+            CK(cudaEventElapsedTime(&ms, ctx->ev_t[1], ctx->ev_t[2]), "cudaEventElapsedTime");
+            ctx->stats.fallback_ms = ms;
+        }
+    }
+    if (a[ACC_STATUS] & ST_NEGATIVE_DEMAND)
+        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "negative demand found in the scenario matrix");
+    const long long sum = (long long)a[ACC_SUM];
+    const long long inf = (long long)a[ACC_INFEASIBLE];
+    if (out_sum) *out_sum = sum;
+    if (out_infeasible) *out_infeasible = inf;
+    if (out_mean) *out_mean = (S - inf) > 0 ? (double)sum / (double)(S - inf) : NAN;
+    return inf > 0 ? CVRPSD_WARN_INFEASIBLE : CVRPSD_OK;
+}
+
+int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind, const int32_t *mu, const int32_t *region,
+                      int32_t n, int64_t S, int64_t ld, int32_t dtype, void *out, void *stream_ptr)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    ctx->err[0] = 0;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    if (kind != CVRPSD_GEN_NORMAL && kind != CVRPSD_GEN_CORRELATED)
+        return fail(ctx, CVRPSD_ERR_ARG, "generator kind %d unknown", kind);
+    if (dtype != CVRPSD_I16 && dtype != CVRPSD_I32) return fail(ctx, CVRPSD_ERR_DTYPE, "dtype %d", dtype);
+    if (n < 1 || n > CVRPSD_MAX_N) return fail(ctx, CVRPSD_ERR_ARG, "n = %d outside 1..%d", n, CVRPSD_MAX_N);
+    if (S < 0 || S > 0xFFFFFFFFLL) return fail(ctx, CVRPSD_ERR_ARG, "S = %lld outside 0..2^32-1", (long long)S);
+    if (ld < S || ld < 1) return fail(ctx, CVRPSD_ERR_ARG, "ld must be >= max(S, 1)");
+    if (!mu || (kind == CVRPSD_GEN_CORRELATED && !region))
+        return fail(ctx, CVRPSD_ERR_ARG, "mu (and region for correlated demands) are required");
+    for (int k = 0; k < n; ++k) {
+        if (mu[k] < 0) return fail(ctx, CVRPSD_ERR_ARG, "mu[%d] < 0", k);
+        if (region && (region[k] < 0 || region[k] > 3)) return fail(ctx, CVRPSD_ERR_ARG, "region[%d] not in 0..3", k);
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (S == 0) return CVRPSD_OK;
+    int rc = check_device_buffer(ctx, out, ((unsigned long long)(n - 1) * ld + S) * dtype, "out");
+    if (rc) return rc;
+    if (!ctx->d_gen) {
+        CK(cudaMalloc(&ctx->d_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMalloc(gen)");
+        CK(cudaMallocHost(&ctx->h_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMallocHost(gen)");
+        CK(cudaEventCreateWithFlags(&ctx->ev_gen, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    CK(cudaEventSynchronize(ctx->ev_gen), "cudaEventSynchronize");
+    for (int k = 0; k < n; ++k) {
+        ctx->h_gen[k] = mu[k];
+        ctx->h_gen[n + k] = region ? region[k] : 0;
+    }
+    CK(cudaMemcpyAsync(ctx->d_gen, ctx->h_gen, 2 * (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
+       "upload mu/region");
+    CK(cudaEventRecord(ctx->ev_gen, stream), "cudaEventRecord");
+    GenParams g{seed, kind, ctx->d_gen, ctx->d_gen + n, n, S, ld, out};
+    CK(launch_gen_demand(g, dtype, stream), "gen_demand launch");
+    return CVRPSD_OK;
+}
+
+}  // extern "C"

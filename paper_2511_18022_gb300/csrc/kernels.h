@@ -1,0 +1,77 @@
+// Internal interface between the C ABI (api.cu) and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cvrpsd {
+
+// Accumulator words written by the Split kernels (device, zeroed per call).
+enum AccWord { ACC_SUM = 0, ACC_INFEASIBLE = 1, ACC_OVERFLOW = 2, ACC_STATUS = 3, ACC_WORDS = 4 };
+
+// Device status bits (ACC_STATUS).
+enum StatusBits { ST_NEGATIVE_DEMAND = 1 };
+
+// One tour position as the kernels read it: the demand row of sigma_i and the
+// scenario-independent cost term C_i (see api.cu: C_i = c(sigma_i,0) +
+// c(0,sigma_{i+1}) - c(sigma_i,sigma_{i+1}) for i < n, and for i = n the full
+// tail D[n] + c(sigma_n, 0)).
+struct TourStep {
+    int32_t row;
+    int32_t c;
+};
+
+struct SplitParams {
+    const TourStep *tab;          // device [n]
+    const void *demand;           // device [n][ld]
+    int64_t ld;                   // row pitch, elements
+    int64_t S;                    // scenarios
+    int32_t n, Q, L;              // L > n means no route-length limit
+    int32_t g0;                   // c(0, sigma_1)
+    uint32_t K;                   // key scale: power of two > n
+    int32_t *out_cost;            // device [S] or nullptr
+    unsigned long long *acc;      // device [ACC_WORDS]
+    int32_t *ovf_list;            // device [S]: scenarios the deque could not hold
+};
+
+struct DequeShape {
+    int threads;    // 64, 128, 256
+    int spt;        // 1, 2
+    int ring;       // 16, 32, 64
+};
+
+// Deque kernel, one thread per `spt` scenarios. esize = 2 or 4.
+cudaError_t launch_split_deque(const SplitParams &p, int esize, const DequeShape &shape,
+                               cudaStream_t stream);
+cudaError_t launch_split_deque_i16_cap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
+cudaError_t launch_split_deque_i16_nocap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
+cudaError_t launch_split_deque_i32_cap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
+cudaError_t launch_split_deque_i32_nocap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
+
+// Rings ([spt][ring][threads] int2) followed by the tour table.
+inline size_t split_deque_smem(const SplitParams &p, const DequeShape &shape)
+{
+    return (size_t)shape.spt * shape.ring * shape.threads * 8 + (size_t)p.n * sizeof(TourStep);
+}
+
+// Warp-per-scenario kernel. If `list` is non-null it evaluates the scenarios
+// named in list[0 .. *count) (count lives on the device); otherwise all S.
+// `max_smem` is the device's opt-in shared memory per block.
+cudaError_t launch_split_warp(const SplitParams &p, int esize, const int32_t *list,
+                              const unsigned long long *count, int grid_ctas, int max_smem,
+                              cudaStream_t stream);
+inline size_t split_warp_smem_per_warp(int n) { return (size_t)2 * (n + 1) * sizeof(int); }
+
+// Scenario generator.
+struct GenParams {
+    uint64_t seed;
+    int32_t kind;
+    const int32_t *mu;            // device [n]
+    const int32_t *region;        // device [n]
+    int32_t n;
+    int64_t S, ld;
+    void *out;
+};
+cudaError_t launch_gen_demand(const GenParams &g, int esize, cudaStream_t stream);
+
+}  // namespace cvrpsd

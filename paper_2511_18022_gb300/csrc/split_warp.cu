@@ -1,0 +1,129 @@
+// Transition-parallel Split: one warp evaluates one scenario (Section 3,
+// "transition-level parallelism"). For each position i the 32 lanes take the
+// candidates p of the feasible window [mask(i), i-1] of Eq. 2/3 in a strided
+// pattern and a warp min-reduction picks the best, so the cost per position
+// is O(|window| / 32 + log 32) and no candidate bound is needed. It serves the
+// scenarios the deque kernel could not hold, and any tour when forced.
+//
+// Per warp, shared memory holds the scenario's prefix loads P[0..n] (demands
+// loaded by all lanes at once, then a warp scan) and the values
+// g[0..n] with g(p) = f(p) + c(0, sigma_{p+1}) - D[p+1] (see split_deque.cuh).
+// The window start mask(i) is the smallest p >= i - L with
+// P(i) - P(p) <= Q, tracked by a pointer that only moves forward.
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace cvrpsd {
+
+template <typename DT>
+__global__ void __launch_bounds__(128) split_warp_kernel(SplitParams p, const int32_t *list,
+                                                         const unsigned long long *count)
+{
+    extern __shared__ __align__(16) int wsmem[];
+    const int n = p.n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    int *P = wsmem + (size_t)w * 2 * (n + 1);
+    int *g = P + (n + 1);
+    const long long total = list ? (long long)*count : p.S;
+    const DT *dem = reinterpret_cast<const DT *>(p.demand);
+    const int Q = p.Q;
+
+    long long sum = 0;
+    unsigned inf = 0, status = 0;
+    for (long long item = (long long)blockIdx.x * wpb + w; item < total;
+         item += (long long)gridDim.x * wpb) {
+        const long long s = list ? (long long)list[item] : item;
+
+        // Demands in tour order, clamped to Q+1 (anything above Q is infeasible).
+        bool neg = false, bad = false;
+        for (int i = 1 + lane; i <= n; i += 32) {
+            int q = (int)dem[(long long)p.tab[i - 1].row * p.ld + s];
+            if (q < 0) { neg = true; q = 0; }
+            if (q > Q) { bad = true; q = Q + 1; }
+            P[i] = q;
+        }
+        __syncwarp();
+        // Inclusive prefix sums, 32 positions at a time.
+        int carry = 0;
+        for (int b = 1; b <= n; b += 32) {
+            const int i = b + lane;
+            int v = i <= n ? P[i] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (i <= n) P[i] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) { P[0] = 0; g[0] = p.g0; }
+        neg = __any_sync(0xffffffffu, neg);
+        bad = __any_sync(0xffffffffu, bad);
+        __syncwarp();
+
+        int cost = INT32_MAX;
+        if (!bad) {
+            int lo = 0;
+            for (int i = 1; i <= n; ++i) {
+                const int Pi = P[i];
+                if (i - lo > p.L) lo = i - p.L;
+                while (Pi - P[lo] > Q) ++lo;            // same on every lane
+                int m = INT32_MAX;
+                for (int c = lo + lane; c < i; c += 32) m = min(m, g[c]);
+                m = __reduce_min_sync(0xffffffffu, m);
+                const int gi = p.tab[i - 1].c + m;
+                if (lane == 0) g[i] = gi;
+                __syncwarp();
+            }
+            cost = g[n];
+        }
+        if (lane == 0) {
+            if (neg) status |= ST_NEGATIVE_DEMAND;
+            if (bad) ++inf; else sum += cost;
+            if (p.out_cost) p.out_cost[s] = cost;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (sum) atomicAdd(p.acc + ACC_SUM, (unsigned long long)sum);
+        if (inf) atomicAdd(p.acc + ACC_INFEASIBLE, (unsigned long long)inf);
+        if (status) atomicOr(p.acc + ACC_STATUS, (unsigned long long)status);
+    }
+}
+
+cudaError_t launch_split_warp(const SplitParams &p, int esize, const int32_t *list,
+                              const unsigned long long *count, int grid_ctas, int max_smem,
+                              cudaStream_t stream)
+{
+    const size_t per_warp = split_warp_smem_per_warp(p.n);
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * per_warp > (size_t)max_smem) --warps;
+    if (per_warp > (size_t)max_smem) return cudaErrorInvalidValue;
+    const int threads = 32 * warps;
+    const size_t smem = (size_t)warps * per_warp;
+    if (esize == 2) {
+        auto k = split_warp_kernel<int16_t>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid_ctas, threads, smem, stream>>>(p, list, count);
+    } else {
+        auto k = split_warp_kernel<int32_t>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid_ctas, threads, smem, stream>>>(p, list, count);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_deque(const SplitParams &p, int esize, const DequeShape &shape,
+                               cudaStream_t stream)
+{
+    const bool cap = p.L < p.n;
+    if (esize == 2) return cap ? launch_split_deque_i16_cap(p, shape, stream)
+                               : launch_split_deque_i16_nocap(p, shape, stream);
+    return cap ? launch_split_deque_i32_cap(p, shape, stream)
+               : launch_split_deque_i32_nocap(p, shape, stream);
+}
+
+}  // namespace cvrpsd
