@@ -176,7 +176,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from synth import workload
-    w = workload(args.workload)
+    w = workload(args.workload, S=args.S or None)
     inst = w.instances[0]
     cores = host_cores()
     cols = args.ref_cols
@@ -208,9 +208,10 @@ def run_reference(args):
 
 
 def workload_config(w, inst) -> dict:
+    gb = inst.n * w.S * 2 / 1e9
     return {"workload": w.name, "n": inst.n, "S": w.S, "Q": inst.Q, "L": inst.L,
             "demand": "correlated lognormal, int16 [n][S]",
-            "l2": "inputs larger than L2 (2.10 GB scenario matrix per step), no flush"}
+            "l2": f"inputs larger than L2 ({gb:.2f} GB scenario matrix per step), no flush"}
 
 
 def run_ours(args):
@@ -224,7 +225,7 @@ def run_ours(args):
     from synth import workload
 
     build.build()
-    w = workload(args.workload)
+    w = workload(args.workload, S=args.S or None)
     inst = w.instances[0]
     n, S = inst.n, w.S
     sp = cv.Splitter(local)
@@ -286,10 +287,11 @@ def run_ours(args):
                 "algorithmic_bytes": algo_bytes}
 
     # end to end from pinned host memory
-    H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
-    H.copy_(D)
-    Hout = torch.empty(S, dtype=torch.int32, pin_memory=True)
-    torch.cuda.synchronize()
+    if args.e2e_steps > 0:
+        H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
+        H.copy_(D)
+        Hout = torch.empty(S, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize()
 
     def e2e_step():
         D.copy_(H, non_blocking=True)
@@ -298,17 +300,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         return res
 
-    e2e_step()
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": n * S * 2, "d2h_bytes_per_step": S * 4 + 24,
-           "steps": args.e2e_steps}
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": n * S * 2, "d2h_bytes_per_step": S * 4 + 24,
+               "steps": args.e2e_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -344,6 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="million-n1000")
+    ap.add_argument("--S", type=int, default=0,
+                    help="scenarios per rank (default: the workload's own); a smaller S gives a "
+                         "scaled-down case of the same generator, e.g. for ncu captures")
     ap.add_argument("--shape", default="", help="threads,spt,ring of the deque kernel")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
