@@ -163,6 +163,37 @@ int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind,
                       int64_t S, int64_t ld, int32_t dtype, void *out,
                       void *stream);
 
+/* Largest S accepted by cvrpsd_split_eval_noalloc. */
+#define CVRPSD_NOALLOC_MAX_S 1048576
+
+/*
+ * cvrpsd_split_eval for callers that cannot allocate device memory when they
+ * call: programs that hand all device memory to their own pool at start-up,
+ * and loops where a cudaMalloc could block on the device or fail under memory
+ * pressure. The paper has no counterpart; this is a deployment variant.
+ *
+ * Same inputs, outputs, conventions and results as cvrpsd_split_eval, on the
+ * current CUDA device and without a context. Its scratch (accumulators, the
+ * tour table, the list of scenarios handed to the warp kernel) is one
+ * file-scope device array of about 4.1 MiB. Every device that loads the
+ * library holds it until the library is unloaded. The call allocates no device memory
+ * (no cudaMalloc, no cudaFree). Limits: 1 <= n <= CVRPSD_MAX_N and
+ * 0 <= S <= CVRPSD_NOALLOC_MAX_S; a larger S returns CVRPSD_ERR_UNSUPPORTED.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and the device limits; make that first call before
+ * any stream capture. Every call on a device shares the one array: each call
+ * clears the accumulators it needs, but two calls whose work overlaps on the
+ * GPU (different streams, or host threads) race on it and must be serialised
+ * by the caller. Errors are returned as codes only (no message).
+ */
+int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n,
+                              const int32_t *dist, const void *demand,
+                              int32_t demand_dtype, int64_t S, int64_t ld,
+                              int32_t Q, int32_t L, int32_t *out_cost,
+                              int64_t *out_sum, int64_t *out_infeasible,
+                              double *out_mean, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
 ]
@@ -134,6 +134,42 @@ def cvrpsd_split_eval(ctx, tour, dist, demand, Q: int, L: int | None = None, *,
     rc = lib.cvrpsd_split_eval(ctx, tour.ctypes.data, n, dist.ctypes.data, dptr, int(dtype),
                                int(S), int(ld), int(Q), L, optr, *hs, _stream_ptr(stream))
     _lib.check(ctx, rc)
+    if not host_outputs:
+        return SplitResult(rc, None, None, None)
+    return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)
+
+
+def cvrpsd_split_eval_noalloc(tour, dist, demand, Q: int, L: int | None = None, *,
+                              S: int | None = None, ld: int | None = None, dtype: int | None = None,
+                              out_cost=None, host_outputs: bool = True, stream=None) -> SplitResult:
+    """Same Split as cvrpsd_split_eval on the current device, for callers that
+    cannot allocate device memory at call time (their memory is all in their
+    own pool, or a cudaMalloc could block or fail mid-loop). Uses the library's
+    fixed device scratch: at most 2^20 scenarios, and calls that overlap on the
+    GPU must be serialised by the caller."""
+    tour = _i32(tour)
+    dist = _i32(dist)
+    n = int(tour.shape[0])
+    dptr, dcode, dshape = _dev(demand)
+    if dshape is not None:
+        if len(dshape) != 2 or dshape[0] != n:
+            raise CvrpsdError(_lib.ERR_ARG, f"demand must be [n][ld] with n={n}, got {dshape}")
+        ld = dshape[1] if ld is None else ld
+        S = ld if S is None else S
+        dtype = dcode if dtype is None else dtype
+        if dtype is None:
+            raise CvrpsdError(_lib.ERR_DTYPE, f"demand must be int16 or int32, got {demand.dtype}")
+    if S is None or ld is None or dtype is None:
+        raise CvrpsdError(_lib.ERR_ARG, "S, ld and dtype are required with a raw demand pointer")
+    optr, _, _ = _dev(out_cost)
+    L = n if L is None else int(L)
+    s_sum, s_inf, s_mean = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    hs = (ctypes.byref(s_sum), ctypes.byref(s_inf), ctypes.byref(s_mean)) if host_outputs else (None,) * 3
+    lib = _lib.load()
+    rc = lib.cvrpsd_split_eval_noalloc(tour.ctypes.data, n, dist.ctypes.data, dptr, int(dtype), int(S),
+                                       int(ld), int(Q), L, optr, *hs, _stream_ptr(stream))
+    if rc < 0:
+        raise CvrpsdError(rc, f"cvrpsd_split_eval_noalloc: {lib.cvrpsd_strerror(rc).decode()}")
     if not host_outputs:
         return SplitResult(rc, None, None, None)
     return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)

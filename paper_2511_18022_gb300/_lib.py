@@ -30,7 +30,9 @@ EXPORTS = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_strerror", "cvrpsd_last_error",
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
+    "cvrpsd_split_eval_noalloc",
 ]
+NOALLOC_MAX_S = 1048576
 
 
 class Config(ctypes.Structure):
@@ -77,6 +79,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_set_profiling.argtypes = [vp, i32]
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_gen_demand.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, i32, i64, i64, i32, vp, vp]
+    lib.cvrpsd_split_eval_noalloc.argtypes = [vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)          # raises AttributeError if a symbol is missing
     if path is None:

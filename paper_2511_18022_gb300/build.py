@@ -24,6 +24,7 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("split_warp.cu", [], "split_warp.o"),
     ("gen_demand.cu", [], "gen_demand.o"),
     ("api.cu", [], "api.o"),
+    ("noalloc.cu", [], "noalloc.o"),
 ]
 
 
