@@ -52,7 +52,7 @@ __device__ __forceinline__ void load_demands(const char *__restrict__ base, int 
                                              bool full, int nvalid, int (&q)[SPT])
 {
     const char *ptr = base + (unsigned long long)(uint32_t)row * ldb;
-    if (full) {
+    if (SPT == 1 || full) {
         using V = typename DemandVec<DT, SPT>::T;
         const V v = __ldcs(reinterpret_cast<const V *>(ptr));
         if constexpr (SPT == 1) {
@@ -74,7 +74,7 @@ struct Deque {
     int fe;            //              route-length expiry step
     int bg;            // back entry: g
     uint32_t hoff;     // byte offset of the front slot within the ring
-    uint32_t toff;     // byte offset of the next free slot
+    uint32_t boff;     // byte offset of the back slot
     uint32_t pk;       // K * prefix load
     uint32_t qmax;     // largest demand seen, as unsigned (negatives are huge)
     bool ovf;          // the ring was too small
@@ -107,39 +107,16 @@ struct Ring {
     __device__ static __forceinline__ uint32_t prev(uint32_t off) { return (off - kStride) & kMask; }
 };
 
-// Drop expired front entries (capacity or route length) at position i. The
-// back entry is always in the window of a feasible scenario, so the walk stops
-// there at the latest. `ring` is the shared address of this scenario's ring.
-template <int R, int T, bool LCAP>
-__device__ __forceinline__ void pop_front(Deque &d, uint32_t ring, int i, uint32_t Km, int L)
-{
-    using RG = Ring<R, T>;
-    const uint32_t last = RG::prev(d.toff);
-    do {
-        if (d.hoff == last) break;
-        d.hoff = RG::next(d.hoff);
-        const int2 e = lds2(ring + d.hoff);
-        d.fg = e.x;
-        d.fx = (uint32_t)e.y;
-        if (LCAP) d.fe = (int)(d.fx & Km) + L + 1;
-    } while ((int)(d.fx - d.pk) < 0 || (LCAP && i >= d.fe));
-}
-
-// Remove back entries not smaller than gi; returns true if the deque emptied.
-template <int R, int T>
-__device__ __forceinline__ bool pop_back(Deque &d, uint32_t ring, int gi)
-{
-    using RG = Ring<R, T>;
-    do {
-        d.toff = RG::prev(d.toff);
-        if (d.toff == d.hoff) return true;      // the front itself was dominated
-        d.bg = lds1(ring + RG::prev(d.toff));
-    } while (d.bg >= gi);
-    return false;
-}
-
 // One position of the walk. PUSH: positions 1..n-1 add candidate i; the last
 // position only reads the window minimum, returned as f(n).
+//
+// Pops at both ends run as warp-uniform loops: every lane executes each
+// iteration (loads included) and applies it only if it still has an entry to
+// drop, so the warp never splits on this data-dependent control flow; the
+// loop ends when no lane has anything left (vote). Each scenario's walk is
+// exactly the sequential deque walk. With C_i > 0 (the usual case; C_i is
+// the same for all scenarios, so the test is uniform) the new value
+// min + C_i exceeds the front and the back pops cannot empty the deque.
 template <int R, int T, bool LCAP, bool PUSH>
 __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, int ci, uint32_t K,
                                        uint32_t xi, int L)
@@ -147,21 +124,52 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
     using RG = Ring<R, T>;
     d.qmax = max(d.qmax, (uint32_t)q);
     d.pk += (uint32_t)q * K;
-    if ((int)(d.fx - d.pk) < 0 || (LCAP && i >= d.fe)) pop_front<R, T, LCAP>(d, ring, i, K - 1, L);
+    // front: drop entries that left the window (never past the back entry)
+    bool pf = (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe))) & (d.hoff != d.boff);
+    while (__any_sync(0xffffffffu, pf)) {
+        const uint32_t nh = RG::next(d.hoff);
+        const int2 e = lds2(ring + nh);
+        d.hoff = pf ? nh : d.hoff;
+        d.fg = pf ? e.x : d.fg;
+        d.fx = pf ? (uint32_t)e.y : d.fx;
+        if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
+        pf = pf & (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe))) & (d.hoff != d.boff);
+    }
     const int gi = d.fg + ci;
     if (!PUSH) return gi;
-    bool empty = false;
-    if (d.bg >= gi) empty = pop_back<R, T>(d, ring, gi);
     const uint32_t x = d.pk + xi;               // K * (P(i) + Q) + i
-    sts2(ring + d.toff, gi, (int)x);
-    if (empty) {                                // the new entry is also the front
-        d.fg = gi;
-        d.fx = x;
-        if (LCAP) d.fe = i + L + 1;
+    bool pb = d.bg >= gi;
+    if (ci > 0) {
+        // back: drop entries not smaller than gi (the front is smaller)
+        while (__any_sync(0xffffffffu, pb)) {
+            const uint32_t bp = RG::prev(d.boff);
+            const int below = lds1(ring + bp);
+            d.boff = pb ? bp : d.boff;
+            d.bg = pb ? below : d.bg;
+            pb = pb & (below >= gi);
+        }
+        d.boff = RG::next(d.boff);
+    } else {
+        // back pops may reach the front: the new entry then becomes the front
+        bool empty = false;
+        while (__any_sync(0xffffffffu, pb)) {
+            const bool emp = d.boff == d.hoff;
+            const uint32_t bp = RG::prev(d.boff);
+            const int below = lds1(ring + bp);
+            empty |= pb & emp;
+            d.boff = pb ? bp : d.boff;
+            d.bg = pb ? below : d.bg;
+            pb = pb & !emp & (below >= gi);
+        }
+        d.boff = RG::next(d.boff);
+        d.hoff = empty ? d.boff : d.hoff;
+        d.fg = empty ? gi : d.fg;
+        d.fx = empty ? x : d.fx;
+        if (LCAP) d.fe = empty ? i + L + 1 : d.fe;
     }
+    sts2(ring + d.boff, gi, (int)x);
     d.bg = gi;
-    d.toff = RG::next(d.toff);
-    d.ovf |= d.toff == d.hoff;                  // ring full: the next push would overwrite the front
+    d.ovf |= RG::next(d.boff) == d.hoff;        // ring full: the next push would overwrite the front
     return gi;
 }
 
@@ -203,17 +211,20 @@ __device__ __forceinline__ void block_accumulate(long long sum, unsigned inf, un
 // Positions of one prefetch block. GUARD: the block may run past n; the last
 // position reads f(n) instead of pushing. `tab` is the shared address of the
 // tour table (TourStep = {row, c}).
+// Positions of one prefetch block. GUARD: the block may run past n; the last
+// position reads f(n) instead of pushing. `tab` is the shared address of the
+// tour table (TourStep = {row, c}).
 template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD>
 __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
                                            uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L,
                                            int (&out)[SPT])
 {
-    const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u;
+    const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u + 4u;
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = i0 + u;
         if (GUARD && i > n) break;
-        const int ci = lds1(t0 + 8u * u + 4u);
+        const int ci = lds1(t0 + 8u * u);
         const uint32_t xi = QK + (uint32_t)i;
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
@@ -223,15 +234,16 @@ __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&rin
     }
 }
 
-template <typename DT, int SPT>
+// Demands of positions i0 .. i0 + kPrefetch - 1. Positions past n re-read row
+// n (in bounds, unused), which keeps the loads free of branches.
+template <typename DT, int SPT, bool CLAMP = true>
 __device__ __forceinline__ void prefetch_block(const char *base, uint32_t tab, int i0, int n, uint32_t ldb,
                                                bool full, int nvalid, int (&q)[kPrefetch][SPT])
 {
-    const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u;
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
-        const int i = i0 + u;
-        if (i <= n) load_demands<DT, SPT>(base, lds1(t0 + 8u * u), ldb, full, nvalid, q[u]);
+        const int i = CLAMP ? min(i0 + u, n) : i0 + u;
+        load_demands<DT, SPT>(base, lds1(tab + (uint32_t)(i - 1) * 8u), ldb, full, nvalid, q[u]);
     }
 }
 
@@ -258,16 +270,17 @@ __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
     const uint32_t K = p.K, QK = (uint32_t)p.Q * p.K;
     const int L = p.L;
 
+    // Every thread walks (threads past S on column 0, results discarded): the
+    // pop loops vote across the full warp.
     long long sum = 0;
-    if (nvalid > 0) {
+    {
         Deque d[SPT];
         uint32_t ring[SPT];
         int out[SPT];
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
             ring[j] = sbase + (uint32_t)j * R * T * 8;
-            d[j].hoff = (uint32_t)tid * 8u;
-            d[j].toff = RG::next(d[j].hoff);
+            d[j].hoff = d[j].boff = (uint32_t)tid * 8u;
             d[j].fg = d[j].bg = p.g0;
             d[j].fx = QK;                           // x(0) = K * (0 + Q) + 0
             d[j].fe = L + 1;
@@ -281,17 +294,22 @@ __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
         int qa[kPrefetch][SPT], qb[kPrefetch][SPT];
         prefetch_block<DT, SPT>(base, tab, 1, n, ldb, full, nvalid, qa);
         int i0 = 1;
-        // Double blocks whose positions are all below n: no guards.
-        for (; i0 + 2 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
-            prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+        // Double blocks whose positions, and those of the next prefetch, are
+        // all below n: no guards or clamps.
+        for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
+            prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
             walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, out);
-            prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+            prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
             walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
         }
-        // The remaining positions i0 .. n.
-        prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, out);
-        if (i0 + kPrefetch <= n) walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+        // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
+        for (; i0 <= n; i0 += 2 * kPrefetch) {
+            prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+            walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, out);
+            if (i0 + kPrefetch > n) break;
+            prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+            walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+        }
 
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
