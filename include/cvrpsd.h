@@ -163,6 +163,58 @@ int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind,
                       int64_t S, int64_t ld, int32_t dtype, void *out,
                       void *stream);
 
+/* ---- Batches of tours: one persistent launch, captured in a CUDA graph ----
+ *
+ * Many giant tours (Section 3; in the paper's setting, the candidate tours a
+ * metaheuristic evaluates), each with its own customers, distances, demand
+ * matrix, Q and L, all under S scenarios. The library packs the tours'
+ * tables, orders the work (largest tours first) and captures the whole
+ * evaluation -- clearing the accumulators, one persistent Split kernel whose
+ * blocks take (tour, scenario tile) items from an atomic counter, the warp
+ * kernel for set-aside scenarios, and the copy of the per-tour sums to pinned
+ * host memory -- into one CUDA graph at creation. */
+typedef struct {
+    const int32_t *tour;   /* HOST [n]: customer ids, a permutation of 1..n */
+    int32_t n;             /* 1 <= n <= CVRPSD_MAX_N */
+    const int32_t *dist;   /* HOST [(n+1)^2], node 0 = depot */
+    const void *demand;    /* DEVICE [n][ld], the batch's demand type */
+    int64_t ld;            /* row pitch in elements, >= S */
+    int32_t Q;             /* capacity >= 0 */
+    int32_t L;             /* route-length limit >= 1 (>= n: none) */
+    int32_t *out_cost;     /* DEVICE [S] or NULL */
+} cvrpsd_tour_desc;
+
+typedef struct cvrpsd_batch cvrpsd_batch;
+
+/* Validate and pack T >= 1 tours, allocate the batch's device scratch and
+ * capture its graph (the launch shape is the context's configuration, or the
+ * default). The host arrays are read only during this call; the device
+ * buffers must stay valid for the batch's lifetime. Errors as for
+ * cvrpsd_split_eval; a bad tour is reported with its index in
+ * cvrpsd_last_error. */
+int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+                        int32_t demand_dtype, cvrpsd_batch **batch);
+
+/* Enqueue one evaluation of the batch (a graph launch) on `stream`. The
+ * demand matrices may change between runs; the tours may not. Runs of one
+ * batch must not overlap. */
+int cvrpsd_batch_run(cvrpsd_batch *batch, void *stream);
+
+/* Wait for the last run and return per-tour results (arrays of T, each may be
+ * NULL): exact sum of feasible costs, infeasible count, mean (NaN if no
+ * scenario is feasible), and a status (0, CVRPSD_WARN_INFEASIBLE or
+ * CVRPSD_ERR_DEVICE_STATUS for a negative demand). Returns the worst
+ * status. */
+int cvrpsd_batch_results(cvrpsd_batch *batch, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
+                         int32_t *out_status);
+
+int cvrpsd_batch_destroy(cvrpsd_batch *batch);
+
+/* One-shot batch: create, run on `stream`, read the results, destroy. */
+int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+                            int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible,
+                            double *out_mean, int32_t *out_status, void *stream);
+
 /* Largest S accepted by cvrpsd_split_eval_noalloc. */
 #define CVRPSD_NOALLOC_MAX_S 1048576
 

@@ -19,7 +19,9 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc",
+    "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
+    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
 ]
@@ -194,6 +196,101 @@ def cvrpsd_gen_demand(ctx, seed: int, kind: int, mu, region, out, *, S: int | No
     _lib.check(ctx, rc)
 
 
+def _tour_descs(tours, S):
+    """ctypes descriptors for a list of dicts with keys tour, dist, demand
+    (CUDA tensor [n][ld]), Q, L (optional), out_cost (optional CUDA int32
+    tensor); also returns the host arrays and device tensors to keep alive."""
+    arr = (_lib.TourDesc * len(tours))()
+    keep, dtype = [], None
+    for k, t in enumerate(tours):
+        tour = _i32(t["tour"])
+        dist = _i32(t["dist"])
+        n = int(tour.shape[0])
+        dptr, dcode, dshape = _dev(t["demand"])
+        if dshape is None or len(dshape) != 2 or dshape[0] != n:
+            raise CvrpsdError(_lib.ERR_ARG, f"tour {k}: demand must be a CUDA tensor [n][ld] with n={n}")
+        if dtype is None:
+            dtype = dcode
+        elif dcode != dtype:
+            raise CvrpsdError(_lib.ERR_DTYPE, f"tour {k}: all demand matrices must share one type")
+        optr, _, _ = _dev(t.get("out_cost"))
+        L = int(t.get("L") or n)
+        arr[k] = _lib.TourDesc(tour.ctypes.data, n, dist.ctypes.data, dptr, int(dshape[1]), int(t["Q"]),
+                               L, optr)
+        keep += [tour, dist, t["demand"], t.get("out_cost")]
+    if dtype is None:
+        raise CvrpsdError(_lib.ERR_DTYPE, "demand must be int16 or int32")
+    return arr, keep, dtype
+
+
+class Batch:
+    """A captured batch of tours (see cvrpsd_batch_create). Keeps the device
+    tensors of its tours alive while it exists."""
+
+    def __init__(self, ctx, tours, S: int):
+        arr, keep, dtype = _tour_descs(tours, S)
+        h = ctypes.c_void_p()
+        lib = _lib.load()
+        _lib.check(ctx, lib.cvrpsd_batch_create(ctx, len(tours), arr, int(S), int(dtype), ctypes.byref(h)))
+        self.ctx, self.handle, self.T, self.S = ctx, h, len(tours), int(S)
+        self._keep = [t for t in keep if t is not None and not isinstance(t, np.ndarray)]
+
+    def run(self, stream=None):
+        _lib.check(self.ctx, _lib.load().cvrpsd_batch_run(self.handle, _stream_ptr(stream)))
+
+    def results(self) -> dict:
+        T = self.T
+        s = np.zeros(T, np.int64)
+        inf = np.zeros(T, np.int64)
+        mean = np.zeros(T, np.float64)
+        st = np.zeros(T, np.int32)
+        rc = _lib.load().cvrpsd_batch_results(self.handle, s.ctypes.data, inf.ctypes.data, mean.ctypes.data,
+                                              st.ctypes.data)
+        _lib.check(self.ctx, rc)
+        return {"status": rc, "sum": s, "infeasible": inf, "mean": mean, "tour_status": st}
+
+    def close(self):
+        if self.handle is not None:
+            _lib.load().cvrpsd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cvrpsd_batch_create(ctx, tours, S: int) -> Batch:
+    return Batch(ctx, tours, S)
+
+
+def cvrpsd_batch_run(batch: Batch, stream=None) -> None:
+    batch.run(stream)
+
+
+def cvrpsd_batch_results(batch: Batch) -> dict:
+    return batch.results()
+
+
+def cvrpsd_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+def cvrpsd_split_eval_batch(ctx, tours, S: int, stream=None) -> dict:
+    """One-shot batch: per-tour exact sums, infeasible counts, means, status."""
+    arr, keep, dtype = _tour_descs(tours, S)
+    T = len(tours)
+    s = np.zeros(T, np.int64)
+    inf = np.zeros(T, np.int64)
+    mean = np.zeros(T, np.float64)
+    st = np.zeros(T, np.int32)
+    rc = _lib.load().cvrpsd_split_eval_batch(ctx, T, arr, int(S), int(dtype), s.ctypes.data, inf.ctypes.data,
+                                             mean.ctypes.data, st.ctypes.data, _stream_ptr(stream))
+    _lib.check(ctx, rc)
+    return {"status": rc, "sum": s, "infeasible": inf, "mean": mean, "tour_status": st}
+
+
 class Splitter:
     """Owns one library context on one device."""
 
@@ -226,3 +323,9 @@ class Splitter:
 
     def gen_demand(self, seed, kind, mu, region, out, **kw):
         cvrpsd_gen_demand(self.ctx, seed, kind, mu, region, out, **kw)
+
+    def batch(self, tours, S) -> Batch:
+        return Batch(self.ctx, tours, S)
+
+    def split_batch(self, tours, S, stream=None) -> dict:
+        return cvrpsd_split_eval_batch(self.ctx, tours, S, stream)

@@ -30,7 +30,8 @@ EXPORTS = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_strerror", "cvrpsd_last_error",
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
-    "cvrpsd_split_eval_noalloc",
+    "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
+    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch",
 ]
 NOALLOC_MAX_S = 1048576
 
@@ -45,6 +46,12 @@ class Stats(ctypes.Structure):
                 ("spt", ctypes.c_int32), ("ring", ctypes.c_int32),
                 ("overflow", ctypes.c_int64), ("launches", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float)]
+
+
+class TourDesc(ctypes.Structure):
+    _fields_ = [("tour", ctypes.c_void_p), ("n", ctypes.c_int32), ("dist", ctypes.c_void_p),
+                ("demand", ctypes.c_void_p), ("ld", ctypes.c_int64), ("Q", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("out_cost", ctypes.c_void_p)]
 
 
 class CvrpsdError(RuntimeError):
@@ -80,6 +87,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_gen_demand.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, i32, i64, i64, i32, vp, vp]
     lib.cvrpsd_split_eval_noalloc.argtypes = [vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.cvrpsd_batch_create.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, ctypes.POINTER(vp)]
+    lib.cvrpsd_batch_run.argtypes = [vp, vp]
+    lib.cvrpsd_batch_results.argtypes = [vp, vp, vp, vp, vp]
+    lib.cvrpsd_batch_destroy.argtypes = [vp]
+    lib.cvrpsd_split_eval_batch.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)          # raises AttributeError if a symbol is missing
     if path is None:

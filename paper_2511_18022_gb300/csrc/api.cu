@@ -6,8 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/cvrpsd.h"
@@ -427,6 +429,257 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
     if (out_infeasible) *out_infeasible = inf;
     if (out_mean) *out_mean = (S - inf) > 0 ? (double)sum / (double)(S - inf) : NAN;
     return inf > 0 ? CVRPSD_WARN_INFEASIBLE : CVRPSD_OK;
+}
+
+}  // extern "C"
+
+struct cvrpsd_batch {
+    cvrpsd_ctx *ctx = nullptr;
+    int T = 0;
+    long long S = 0;
+    BatchParams bp{};
+    TourDev *d_tours = nullptr;
+    TourStep *d_tabs = nullptr;
+    int2 *d_items = nullptr;
+    unsigned long long *d_acc = nullptr;
+    int2 *d_list = nullptr;
+    unsigned long long *h_acc = nullptr;   // pinned: header + 3 words per tour
+    size_t acc_words = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool ran = false;
+};
+
+namespace {
+
+void batch_free(cvrpsd_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->d_tours) cudaFree(b->d_tours);
+    if (b->d_tabs) cudaFree(b->d_tabs);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_acc) cudaFree(b->d_acc);
+    if (b->d_list) cudaFree(b->d_list);
+    if (b->h_acc) cudaFreeHost(b->h_acc);
+    delete b;
+}
+
+bool valid_batch_shape(const DequeShape &s)
+{
+    return (s.threads == 128 || s.threads == 256) &&
+           ((s.spt == 1 && (s.ring == 16 || s.ring == 32)) || (s.spt == 2 && s.ring == 16));
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S, int32_t demand_dtype,
+                        cvrpsd_batch **out)
+{
+    if (!ctx || !out) return CVRPSD_ERR_ARG;
+    *out = nullptr;
+    ctx->err[0] = 0;
+    if (T < 1 || !tours) return fail(ctx, CVRPSD_ERR_ARG, "T = %d tours (need >= 1)", T);
+    if (demand_dtype != CVRPSD_I16 && demand_dtype != CVRPSD_I32)
+        return fail(ctx, CVRPSD_ERR_DTYPE, "demand_dtype %d", demand_dtype);
+    if (S < 1 || S > INT32_MAX) return fail(ctx, CVRPSD_ERR_ARG, "S = %lld outside 1..2^31-1", (long long)S);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+
+    std::vector<TourDev> hd((size_t)T);
+    std::vector<long long> tab_off((size_t)T);
+    long long total_n = 0;
+    int max_n = 0;
+    bool lcap = false;
+    for (int t = 0; t < T; ++t) {
+        const cvrpsd_tour_desc &d = tours[t];
+        if (d.n < 1 || d.n > CVRPSD_MAX_N) return fail(ctx, CVRPSD_ERR_ARG, "tour %d: n = %d", t, d.n);
+        if (d.Q < 0 || d.L < 1) return fail(ctx, CVRPSD_ERR_ARG, "tour %d: Q = %d, L = %d", t, d.Q, d.L);
+        if (d.ld < S) return fail(ctx, CVRPSD_ERR_ARG, "tour %d: ld = %lld < S", t, (long long)d.ld);
+        if ((unsigned long long)d.ld * demand_dtype > 0xFFFFFFFFull)
+            return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "tour %d: row pitch exceeds 4 GiB", t);
+        int rc = check_device_buffer(ctx, d.demand, ((unsigned long long)(d.n - 1) * d.ld + S) * demand_dtype,
+                                     "demand");
+        if (rc) return fail(ctx, rc, "tour %d: %s", t, std::string(ctx->err).c_str());
+        if (d.out_cost) {
+            rc = check_device_buffer(ctx, d.out_cost, (unsigned long long)S * 4, "out_cost");
+            if (rc) return fail(ctx, rc, "tour %d: %s", t, std::string(ctx->err).c_str());
+        }
+        tab_off[t] = total_n;
+        total_n += d.n;
+        if (d.n > max_n) max_n = d.n;
+        const int L = d.L > d.n ? d.n : d.L;
+        if (L < d.n) lcap = true;
+    }
+    std::vector<TourStep> htab((size_t)total_n);
+    for (int t = 0; t < T; ++t) {
+        const cvrpsd_tour_desc &d = tours[t];
+        int32_t g0 = 0;
+        int rc = build_tour_table(ctx, d.tour, d.n, d.dist, d.Q, htab.data() + tab_off[t], &g0);
+        if (rc) return fail(ctx, rc, "tour %d: %s", t, std::string(ctx->err).c_str());
+        TourDev &td = hd[t];
+        td.tab = nullptr;   // set after upload
+        td.demand = d.demand;
+        td.ld = d.ld;
+        td.out_cost = d.out_cost;
+        td.n = d.n;
+        td.Q = d.Q;
+        td.L = d.L > d.n ? d.n : d.L;
+        if (!lcap) td.L = d.n + 1;
+        td.g0 = g0;
+        td.K = key_scale(d.n);
+        td.pad = 0;
+    }
+
+    DequeShape shape{256, 1, 16};
+    if (ctx->cfg.threads) {
+        DequeShape want{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
+        if (valid_batch_shape(want)) shape = want;
+    }
+    while (split_batch_smem(max_n, shape) > (size_t)ctx->max_smem) {
+        if (shape.spt > 1) shape.spt = 1;
+        else if (shape.ring > 16) shape.ring = 16;
+        else if (shape.threads > 128) shape.threads = 128;
+        else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "tour of %d customers does not fit shared memory", max_n);
+    }
+    const long long per_tile = (long long)shape.threads * shape.spt;
+    const long long tiles = (S + per_tile - 1) / per_tile;
+    if (tiles * T > INT32_MAX) return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "too many work items");
+    // Work items: tours by decreasing n (longest first), all tiles of a tour together.
+    std::vector<int> order((size_t)T);
+    for (int t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tours[a].n > tours[b].n; });
+    std::vector<int2> items((size_t)(tiles * T));
+    size_t k = 0;
+    for (int t : order)
+        for (long long j = 0; j < tiles; ++j) items[k++] = make_int2(t, (int)j);
+
+    cvrpsd_batch *b = new (std::nothrow) cvrpsd_batch();
+    if (!b) return CVRPSD_ERR_NOMEM;
+    b->ctx = ctx;
+    b->T = T;
+    b->S = S;
+    b->acc_words = BACC_WORDS + 3 * (size_t)T;
+    const long long list_cap = std::min<long long>((long long)T * S, 1LL << 24);
+#define BK(call, what)                              do {                                                cudaError_t e_ = (call);                        if (e_ != cudaSuccess) {                            int rc_ = cuda_fail(ctx, e_, what);             cudaGetLastError();                             batch_free(b);                                  return rc_;                                 }                                           } while (0)
+    BK(cudaMalloc(&b->d_tours, sizeof(TourDev) * T), "cudaMalloc(tours)");
+    BK(cudaMalloc(&b->d_tabs, sizeof(TourStep) * total_n), "cudaMalloc(tables)");
+    BK(cudaMalloc(&b->d_items, sizeof(int2) * items.size()), "cudaMalloc(items)");
+    BK(cudaMalloc(&b->d_acc, sizeof(unsigned long long) * b->acc_words), "cudaMalloc(acc)");
+    BK(cudaMalloc(&b->d_list, sizeof(int2) * list_cap), "cudaMalloc(list)");
+    BK(cudaMallocHost(&b->h_acc, sizeof(unsigned long long) * b->acc_words), "cudaMallocHost(acc)");
+    for (int t = 0; t < T; ++t) hd[t].tab = b->d_tabs + tab_off[t];
+    BK(cudaMemcpy(b->d_tours, hd.data(), sizeof(TourDev) * T, cudaMemcpyHostToDevice), "upload tours");
+    BK(cudaMemcpy(b->d_tabs, htab.data(), sizeof(TourStep) * total_n, cudaMemcpyHostToDevice), "upload tables");
+    BK(cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "upload items");
+
+    BatchParams &bp = b->bp;
+    bp.tours = b->d_tours;
+    bp.items = b->d_items;
+    bp.n_items = (int)items.size();
+    bp.S = S;
+    bp.acc = b->d_acc;
+    bp.list = b->d_list;
+    bp.list_cap = list_cap;
+    bp.max_n = max_n;
+    int per_sm = 0;
+    BK(launch_split_batch(bp, demand_dtype, lcap, shape, 0, true, &per_sm, nullptr), "configure batch kernel");
+    if (per_sm < 1) per_sm = 1;
+    const int grid = ctx->sm_count * per_sm;
+    const int warp_grid = 2 * ctx->sm_count;
+    BK(launch_split_warp_batch(bp, demand_dtype, warp_grid, ctx->max_smem, true, nullptr), "configure warp kernel");
+
+    BK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    BK(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "cudaEventCreate");
+    BK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e1 = cudaMemsetAsync(b->d_acc, 0, sizeof(unsigned long long) * b->acc_words, b->cap_stream);
+    cudaError_t e2 = launch_split_batch(bp, demand_dtype, lcap, shape, grid, false, nullptr, b->cap_stream);
+    cudaError_t e3 = launch_split_warp_batch(bp, demand_dtype, warp_grid, ctx->max_smem, false, b->cap_stream);
+    cudaError_t e4 = cudaMemcpyAsync(b->h_acc, b->d_acc, sizeof(unsigned long long) * b->acc_words,
+                                     cudaMemcpyDeviceToHost, b->cap_stream);
+    cudaError_t e5 = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    BK(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4 != cudaSuccess ? e4 : e5,
+       "capture batch graph");
+    BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate batch graph");
+#undef BK
+    ctx->stats = cvrpsd_stats{};
+    ctx->stats.kernel = CVRPSD_KERNEL_DEQUE;
+    ctx->stats.threads = shape.threads;
+    ctx->stats.spt = shape.spt;
+    ctx->stats.ring = shape.ring;
+    ctx->stats.overflow = -1;
+    ctx->stats.launches = 2;
+    ctx->stats.kernel_ms = ctx->stats.fallback_ms = -1.0f;
+    *out = b;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_batch_run(cvrpsd_batch *b, void *stream_ptr)
+{
+    if (!b) return CVRPSD_ERR_ARG;
+    cvrpsd_ctx *ctx = b->ctx;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaGraphLaunch(b->exec, stream), "cudaGraphLaunch");
+    CK(cudaEventRecord(b->done, stream), "cudaEventRecord");
+    b->ran = true;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_batch_results(cvrpsd_batch *b, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
+                         int32_t *out_status)
+{
+    if (!b) return CVRPSD_ERR_ARG;
+    cvrpsd_ctx *ctx = b->ctx;
+    if (!b->ran) return fail(ctx, CVRPSD_ERR_ARG, "batch has not been run");
+    CK(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+    const unsigned long long *h = b->h_acc;
+    if (h[BACC_STATUS] & BST_LIST_FULL)
+        return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "more than %lld set-aside scenarios", (long long)b->bp.list_cap);
+    ctx->stats.overflow = (int64_t)h[BACC_LIST];
+    int worst = CVRPSD_OK;
+    for (int t = 0; t < b->T; ++t) {
+        const unsigned long long *w = h + BACC_WORDS + 3 * t;
+        const long long sum = (long long)w[0], inf = (long long)w[1];
+        int st = CVRPSD_OK;
+        if (w[2] & ST_NEGATIVE_DEMAND) st = CVRPSD_ERR_DEVICE_STATUS;
+        else if (inf > 0) st = CVRPSD_WARN_INFEASIBLE;
+        if (out_sum) out_sum[t] = sum;
+        if (out_infeasible) out_infeasible[t] = inf;
+        if (out_mean) out_mean[t] = (b->S - inf) > 0 ? (double)sum / (double)(b->S - inf) : NAN;
+        if (out_status) out_status[t] = st;
+        if (st < 0) worst = st;
+        else if (worst >= 0 && st > worst) worst = st;
+    }
+    if (worst == CVRPSD_ERR_DEVICE_STATUS) fail(ctx, worst, "negative demand in at least one tour's matrix");
+    return worst;
+}
+
+int cvrpsd_batch_destroy(cvrpsd_batch *b)
+{
+    if (!b) return CVRPSD_ERR_ARG;
+    cudaSetDevice(b->ctx->device);
+    batch_free(b);
+    return CVRPSD_OK;
+}
+
+int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+                            int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
+                            int32_t *out_status, void *stream)
+{
+    cvrpsd_batch *b = nullptr;
+    int rc = cvrpsd_batch_create(ctx, T, tours, S, demand_dtype, &b);
+    if (rc) return rc;
+    rc = cvrpsd_batch_run(b, stream);
+    if (rc == CVRPSD_OK) rc = cvrpsd_batch_results(b, out_sum, out_infeasible, out_mean, out_status);
+    cvrpsd_batch_destroy(b);
+    return rc;
 }
 
 int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind, const int32_t *mu, const int32_t *region,

@@ -62,6 +62,51 @@ cudaError_t launch_split_warp(const SplitParams &p, int esize, const int32_t *li
                               cudaStream_t stream);
 inline size_t split_warp_smem_per_warp(int n) { return (size_t)2 * (n + 1) * sizeof(int); }
 
+// ---- batches of tours (one persistent launch) ----
+
+// One tour of a batch, as the batch kernels read it.
+struct TourDev {
+    const TourStep *tab;          // device [n]
+    const void *demand;           // device [n][ld]
+    long long ld;
+    int32_t *out_cost;            // device [S] or nullptr
+    int32_t n, Q, L, g0;          // L > n: no route-length limit
+    uint32_t K;
+    int32_t pad;
+};
+
+// Batch accumulator header; per tour three words follow: sum, infeasible
+// count, status bits.
+enum BatchAccWord { BACC_COUNTER = 0, BACC_LIST = 1, BACC_STATUS = 2, BACC_WORDS = 4 };
+enum BatchStatusBits { BST_LIST_FULL = 1 };
+
+struct BatchParams {
+    const TourDev *tours;         // device [T]
+    const int2 *items;            // device [n_items]: (tour, scenario tile), in processing order
+    int n_items;
+    long long S;                  // scenarios per tour
+    unsigned long long *acc;      // device [BACC_WORDS + 3 T]
+    int2 *list;                   // device [list_cap]: set-aside (tour, scenario)
+    long long list_cap;
+    int max_n;                    // largest tour (shared-memory table size)
+};
+
+inline size_t split_batch_smem(int max_n, const DequeShape &shape)
+{
+    return (size_t)shape.spt * shape.ring * shape.threads * 8 + (size_t)max_n * sizeof(TourStep);
+}
+// Persistent deque kernel over all work items; with configure_only it only
+// sets the kernel's shared-memory limit (call before stream capture) and
+// reports blocks per SM in *blocks_per_sm.
+cudaError_t launch_split_batch(const BatchParams &b, int esize, bool lcap, const DequeShape &shape, int grid,
+                               bool configure_only, int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i16(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
+                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
+                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_warp_batch(const BatchParams &b, int esize, int grid_ctas, int max_smem, bool configure_only,
+                                    cudaStream_t stream);
+
 // Scenario generator.
 struct GenParams {
     uint64_t seed;

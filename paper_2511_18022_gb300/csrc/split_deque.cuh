@@ -247,10 +247,82 @@ __device__ __forceinline__ void prefetch_block(const char *base, uint32_t tab, i
     }
 }
 
+// The walk of one thread: SPT adjacent scenarios s_first.. of one tour whose
+// table (TourStep = {row, c}) is at shared address `tab`; the rings start at
+// shared address `rings`. Writes f(n) of feasible scenarios to out_cost (if
+// given), returns the sum of those costs, and passes every scenario it sets
+// aside to `set_aside(s)`. Threads with no scenario (s_first >= S) walk
+// column 0 and report nothing: every lane must take part in the pop votes.
+template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside>
+__device__ __forceinline__ long long split_thread(const void *demand, long long ld, long long S, long long s_first,
+                                                  int n, int Q, int L, uint32_t K, int g0, uint32_t rings,
+                                                  uint32_t tab, int tid, int32_t *out_cost, SetAside set_aside)
+{
+    using RG = Ring<R, T>;
+    const long long rem = S - s_first;
+    const bool full = rem >= SPT;
+    const int nvalid = rem >= SPT ? SPT : (int)(rem > 0 ? rem : 0);
+    const uint32_t ldb = (uint32_t)(ld * (long long)sizeof(DT));
+    const char *base = reinterpret_cast<const char *>(demand) + (nvalid ? s_first : 0) * (long long)sizeof(DT);
+    const uint32_t QK = (uint32_t)Q * K;
+
+    Deque d[SPT];
+    uint32_t ring[SPT];
+    int out[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        ring[j] = rings + (uint32_t)j * R * T * 8;
+        d[j].hoff = d[j].boff = (uint32_t)tid * 8u;
+        d[j].fg = d[j].bg = g0;
+        d[j].fx = QK;                               // x(0) = K * (0 + Q) + 0
+        d[j].fe = L + 1;
+        d[j].pk = 0;
+        d[j].qmax = 0;
+        d[j].ovf = false;
+        out[j] = 0;
+        sts2(ring[j] + d[j].hoff, g0, (int)QK);
+    }
+
+    int qa[kPrefetch][SPT], qb[kPrefetch][SPT];
+    prefetch_block<DT, SPT>(base, tab, 1, n, ldb, full, nvalid, qa);
+    int i0 = 1;
+    // Double blocks whose positions, and those of the next prefetch, are all
+    // below n: no guards or clamps.
+    for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
+        prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, out);
+        prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+    }
+    // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
+    for (; i0 <= n; i0 += 2 * kPrefetch) {
+        prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, out);
+        if (i0 + kPrefetch > n) break;
+        prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+    }
+
+    long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        if (j >= nvalid) continue;
+        const long long s = s_first + j;
+        if (d[j].ovf || d[j].qmax > (uint32_t)Q) {
+            // deque too small, a demand above Q, or a negative demand: the
+            // warp kernel evaluates (and classifies) this scenario
+            set_aside(s);
+            continue;
+        }
+        sum += out[j];
+        if (out_cost) out_cost[s] = out[j];
+    }
+    return sum;
+}
+
 template <typename DT, int SPT, int R, int T, bool LCAP>
 __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
 {
-    using RG = Ring<R, T>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = p.n;
     // rings first (SPT regions of R*T*8 bytes), then the tour table
@@ -260,72 +332,15 @@ __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
     __syncthreads();
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t tab = sbase + (uint32_t)SPT * R * T * 8;
-
     const long long s_first = ((long long)blockIdx.x * T + tid) * SPT;
-    const long long rem = p.S - s_first;
-    const bool full = rem >= SPT;
-    const int nvalid = rem >= SPT ? SPT : (int)(rem > 0 ? rem : 0);
-    const uint32_t ldb = (uint32_t)(p.ld * (long long)sizeof(DT));
-    const char *base = reinterpret_cast<const char *>(p.demand) + (nvalid ? s_first : 0) * (long long)sizeof(DT);
-    const uint32_t K = p.K, QK = (uint32_t)p.Q * p.K;
-    const int L = p.L;
-
-    // Every thread walks (threads past S on column 0, results discarded): the
-    // pop loops vote across the full warp.
-    long long sum = 0;
-    {
-        Deque d[SPT];
-        uint32_t ring[SPT];
-        int out[SPT];
-#pragma unroll
-        for (int j = 0; j < SPT; ++j) {
-            ring[j] = sbase + (uint32_t)j * R * T * 8;
-            d[j].hoff = d[j].boff = (uint32_t)tid * 8u;
-            d[j].fg = d[j].bg = p.g0;
-            d[j].fx = QK;                           // x(0) = K * (0 + Q) + 0
-            d[j].fe = L + 1;
-            d[j].pk = 0;
-            d[j].qmax = 0;
-            d[j].ovf = false;
-            out[j] = 0;
-            sts2(ring[j] + d[j].hoff, p.g0, (int)QK);
-        }
-
-        int qa[kPrefetch][SPT], qb[kPrefetch][SPT];
-        prefetch_block<DT, SPT>(base, tab, 1, n, ldb, full, nvalid, qa);
-        int i0 = 1;
-        // Double blocks whose positions, and those of the next prefetch, are
-        // all below n: no guards or clamps.
-        for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
-            prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-            walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, out);
-            prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-            walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
-        }
-        // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
-        for (; i0 <= n; i0 += 2 * kPrefetch) {
-            prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-            walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, out);
-            if (i0 + kPrefetch > n) break;
-            prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-            walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
-        }
-
-#pragma unroll
-        for (int j = 0; j < SPT; ++j) {
-            if (j >= nvalid) continue;
-            const long long s = s_first + j;
-            if (d[j].ovf || d[j].qmax > (uint32_t)p.Q) {
-                // deque too small, a demand above Q, or a negative demand:
-                // the warp kernel evaluates (and classifies) this scenario
-                const unsigned long long idx = atomicAdd(p.acc + ACC_OVERFLOW, 1ull);
-                p.ovf_list[idx] = (int32_t)s;
-                continue;
-            }
-            sum += out[j];
-            if (p.out_cost) p.out_cost[s] = out[j];
-        }
-    }
+    unsigned long long *acc = p.acc;
+    int32_t *list = p.ovf_list;
+    const long long sum = split_thread<DT, SPT, R, T, LCAP>(
+        p.demand, p.ld, p.S, s_first, n, p.Q, p.L, p.K, p.g0, sbase, tab, tid, p.out_cost,
+        [acc, list](long long s) {
+            const unsigned long long idx = atomicAdd(acc + ACC_OVERFLOW, 1ull);
+            list[idx] = (int32_t)s;
+        });
     block_accumulate(sum, 0u, 0u, p.acc);
 }
 

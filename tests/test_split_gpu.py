@@ -234,11 +234,12 @@ def test_argument_errors(sp, cv):
         args.update(kw)
         with pytest.raises(cv.CvrpsdError):
             sp.split(args["tour"], args["dist"], args["demand"], args["Q"], args["L"], **extra)
-    small = torch.empty(50, dtype=torch.int32, device="cuda")[:10]
-    # a view whose allocation is big enough is accepted; a raw pointer past the end is not
-    with pytest.raises(cv.CvrpsdError):
+    # a host address passed as a device buffer is refused before any launch
+    host_out = np.zeros(100, np.int32)
+    with pytest.raises(cv.CvrpsdError) as e:
         sp.split(inst.tour, inst.dist, D.data_ptr(), 30, 20, S=100, ld=100, dtype=cv.I16,
-                 out_cost=small.data_ptr() + 4 * 10**9)
+                 out_cost=host_out.ctypes.data)
+    assert e.value.code == -1
 
 
 # ------------------------------------------------------------ generator
