@@ -163,6 +163,31 @@ int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind,
                       int64_t S, int64_t ld, int32_t dtype, void *out,
                       void *stream);
 
+/* ---- Autotuning the launch shape ---- */
+typedef struct {
+    cvrpsd_config best;     /* fastest shape; also set as the context's configuration */
+    float best_ms;          /* its device time per Split (main kernel + set-aside pass) */
+    int32_t best_dtype;     /* CVRPSD_I16 or CVRPSD_I32: the faster demand storage, timed on a
+                               sample of min(S, 65536) scenarios (int16 only if every demand fits) */
+    int32_t shapes_timed;   /* shapes swept by this call; 0 when the result came from the cache */
+} cvrpsd_tune_result;
+
+/*
+ * Time every launch shape of the scenario-parallel kernel (threads x spt x
+ * ring, see cvrpsd_config) on this workload with CUDA events on `stream`,
+ * check that each shape gives exactly the sum and infeasible count of the
+ * default shape (CVRPSD_ERR_DEVICE_STATUS otherwise), and keep the fastest.
+ * Arguments as for cvrpsd_split_eval; out_cost is not written. With
+ * cache_path != NULL, a result stored under the same key (GPU name, n rounded
+ * up to a power of two, S rounded down to a power of two, demand type,
+ * whether L limits routes) is reused, and a new result is appended to that
+ * file (one JSON object per line). Allocates temporary device buffers for the
+ * demand-type comparison. Synchronous.
+ */
+int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
+                    int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, const char *cache_path,
+                    cvrpsd_tune_result *result, void *stream);
+
 /* ---- Batches of tours: one persistent launch, captured in a CUDA graph ----
  *
  * Many giant tours (Section 3; in the paper's setting, the candidate tours a

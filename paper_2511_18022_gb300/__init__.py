@@ -21,7 +21,7 @@ __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
     "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
-    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
 ]
@@ -196,6 +196,28 @@ def cvrpsd_gen_demand(ctx, seed: int, kind: int, mu, region, out, *, S: int | No
     _lib.check(ctx, rc)
 
 
+def cvrpsd_autotune(ctx, tour, dist, demand, Q: int, L: int | None = None, *, S: int | None = None,
+                    cache_path: str | None = None, stream=None) -> dict:
+    """Time every launch shape on this workload, keep the fastest on the
+    context (see include/cvrpsd.h); returns the chosen shape and timings."""
+    tour = _i32(tour)
+    dist = _i32(dist)
+    n = int(tour.shape[0])
+    dptr, dcode, dshape = _dev(demand)
+    if dshape is None or len(dshape) != 2 or dshape[0] != n or dcode is None:
+        raise CvrpsdError(_lib.ERR_ARG, "demand must be a CUDA int16/int32 tensor [n][ld]")
+    ld = dshape[1]
+    S = ld if S is None else S
+    res = _lib.TuneResult()
+    rc = _lib.load().cvrpsd_autotune(ctx, tour.ctypes.data, n, dist.ctypes.data, dptr, int(dcode), int(S),
+                                     int(ld), int(Q), int(L or n),
+                                     None if cache_path is None else str(cache_path).encode(),
+                                     ctypes.byref(res), _stream_ptr(stream))
+    _lib.check(ctx, rc)
+    return {"threads": res.best.threads, "spt": res.best.spt, "ring": res.best.ring,
+            "ms": res.best_ms, "dtype": res.best_dtype, "shapes_timed": res.shapes_timed}
+
+
 def _tour_descs(tours, S):
     """ctypes descriptors for a list of dicts with keys tour, dist, demand
     (CUDA tensor [n][ld]), Q, L (optional), out_cost (optional CUDA int32
@@ -323,6 +345,9 @@ class Splitter:
 
     def gen_demand(self, seed, kind, mu, region, out, **kw):
         cvrpsd_gen_demand(self.ctx, seed, kind, mu, region, out, **kw)
+
+    def autotune(self, tour, dist, demand, Q, L=None, **kw) -> dict:
+        return cvrpsd_autotune(self.ctx, tour, dist, demand, Q, L, **kw)
 
     def batch(self, tours, S) -> Batch:
         return Batch(self.ctx, tours, S)

@@ -31,7 +31,7 @@ EXPORTS = [
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
     "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
-    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch",
+    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch", "cvrpsd_autotune",
 ]
 NOALLOC_MAX_S = 1048576
 
@@ -46,6 +46,11 @@ class Stats(ctypes.Structure):
                 ("spt", ctypes.c_int32), ("ring", ctypes.c_int32),
                 ("overflow", ctypes.c_int64), ("launches", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", Config), ("best_ms", ctypes.c_float), ("best_dtype", ctypes.c_int32),
+                ("shapes_timed", ctypes.c_int32)]
 
 
 class TourDesc(ctypes.Structure):
@@ -87,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_gen_demand.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, i32, i64, i64, i32, vp, vp]
     lib.cvrpsd_split_eval_noalloc.argtypes = [vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.cvrpsd_autotune.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, ctypes.c_char_p,
+                                    ctypes.POINTER(TuneResult), vp]
     lib.cvrpsd_batch_create.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, ctypes.POINTER(vp)]
     lib.cvrpsd_batch_run.argtypes = [vp, vp]
     lib.cvrpsd_batch_results.argtypes = [vp, vp, vp, vp, vp]

@@ -433,6 +433,172 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
 
 }  // extern "C"
 
+namespace {
+
+// One split with the given shape; the main-kernel + set-aside device time.
+int timed_split(cvrpsd_ctx *ctx, const cvrpsd_config &cfg, const int32_t *tour, int32_t n, const int32_t *dist,
+                const void *demand, int32_t dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, void *stream,
+                long long *sum, long long *inf, float *ms)
+{
+    ctx->cfg = cfg;
+    int64_t s64 = 0, i64 = 0;
+    double mean = 0;
+    const int rc = cvrpsd_split_eval(ctx, tour, n, dist, demand, dtype, S, ld, Q, L, nullptr, &s64, &i64, &mean,
+                                     stream);
+    if (rc < 0) return rc;
+    *sum = s64;
+    *inf = i64;
+    *ms = ctx->stats.kernel_ms + (ctx->stats.fallback_ms > 0 ? ctx->stats.fallback_ms : 0.0f);
+    return CVRPSD_OK;
+}
+
+std::string tune_key(cvrpsd_ctx *ctx, int n, long long S, int dtype, bool lcap)
+{
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "unknown";
+    for (char &c : name)
+        if (c == ' ' || c == '"') c = '_';
+    long long nb = 1, sb = 1;
+    while (nb < n) nb <<= 1;
+    while (sb * 2 <= S) sb <<= 1;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s/n%lld/S%lld/%s/%s", name.c_str(), nb, sb, dtype == CVRPSD_I16 ? "i16" : "i32",
+             lcap ? "cap" : "nocap");
+    return buf;
+}
+
+bool tune_cache_lookup(const char *path, const std::string &key, cvrpsd_tune_result *r)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512], k[256];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        cvrpsd_tune_result t{};
+        if (sscanf(line, "{\"key\": \"%255[^\"]\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"ms\": %f, "
+                         "\"dtype\": %d}",
+                   k, &t.best.threads, &t.best.spt, &t.best.ring, &t.best_ms, &t.best_dtype) == 6 &&
+            key == k && valid_shape(t.best.threads, t.best.spt, t.best.ring)) {
+            t.best.kernel = CVRPSD_KERNEL_DEQUE;
+            *r = t;
+            found = true;   // the last entry for a key wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+}  // namespace
+
+extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist,
+                               const void *demand, int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L,
+                               const char *cache_path, cvrpsd_tune_result *result, void *stream_ptr)
+{
+    if (!ctx || !result) return CVRPSD_ERR_ARG;
+    if (S < 1) return fail(ctx, CVRPSD_ERR_ARG, "autotune needs S >= 1");
+    const cvrpsd_config saved = ctx->cfg;
+    const int saved_prof = ctx->profiling;
+    int rc = cvrpsd_set_profiling(ctx, 1);
+    if (rc) return rc;
+    const bool lcap = L < n;
+    const std::string key = tune_key(ctx, n, S, demand_dtype, lcap);
+    cvrpsd_tune_result best{};
+    long long ref_sum = 0, ref_inf = 0, s_ = 0, i_ = 0;
+    float ms = 0;
+    // reference: the default shape (also validates every argument)
+    rc = timed_split(ctx, cvrpsd_config{CVRPSD_KERNEL_DEQUE, 0, 0, 0}, tour, n, dist, demand, demand_dtype, S, ld,
+                     Q, L, stream_ptr, &ref_sum, &ref_inf, &ms);
+    if (rc < 0) {
+        ctx->cfg = saved;
+        ctx->profiling = saved_prof;
+        return rc;
+    }
+    if (cache_path && tune_cache_lookup(cache_path, key, &best)) {
+        best.shapes_timed = 0;
+        ctx->cfg = best.best;
+        ctx->profiling = saved_prof;
+        *result = best;
+        return CVRPSD_OK;
+    }
+    best.best_ms = 1e30f;
+    int timed = 0;
+    for (int threads : {64, 128, 256})
+        for (int spt : {1, 2})
+            for (int ring : {16, 32, 64}) {
+                const cvrpsd_config cfg{CVRPSD_KERNEL_DEQUE, threads, spt, ring};
+                float t_best = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    rc = timed_split(ctx, cfg, tour, n, dist, demand, demand_dtype, S, ld, Q, L, stream_ptr, &s_,
+                                     &i_, &ms);
+                    if (rc < 0) break;
+                    if (s_ != ref_sum || i_ != ref_inf) {
+                        ctx->cfg = saved;
+                        ctx->profiling = saved_prof;
+                        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "shape %d/%d/%d gives sum %lld, default %lld",
+                                    threads, spt, ring, s_, ref_sum);
+                    }
+                    if (rep > 0 && ms < t_best) t_best = ms;   // first run warms up
+                }
+                if (rc < 0) continue;                            // shape not launchable here
+                ++timed;
+                // the shape the library actually ran (it may shrink spt / threads to fit)
+                const cvrpsd_config ran{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring};
+                if (t_best < best.best_ms) {
+                    best.best_ms = t_best;
+                    best.best = ran;
+                }
+            }
+    if (!timed) {
+        ctx->cfg = saved;
+        ctx->profiling = saved_prof;
+        return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "no launch shape could run this workload");
+    }
+    best.shapes_timed = timed;
+    best.best_dtype = demand_dtype;
+
+    // Demand storage: time the best shape on int16 and int32 copies of a sample.
+    const long long Ss = S < 65536 ? S : 65536;
+    void *tmp[2] = {nullptr, nullptr};
+    unsigned int *sat = nullptr;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    if (cudaMalloc(&tmp[0], (size_t)n * Ss * 2) == cudaSuccess && cudaMalloc(&tmp[1], (size_t)n * Ss * 4) == cudaSuccess &&
+        cudaMalloc(&sat, sizeof(unsigned int)) == cudaSuccess && cudaMemsetAsync(sat, 0, 4, stream) == cudaSuccess &&
+        launch_convert_demand(demand, demand_dtype, ld, tmp[0], 2, Ss, n, Ss, sat, stream) == cudaSuccess &&
+        launch_convert_demand(demand, demand_dtype, ld, tmp[1], 4, Ss, n, Ss, sat, stream) == cudaSuccess) {
+        unsigned int h_sat = 1;
+        cudaMemcpyAsync(&h_sat, sat, 4, cudaMemcpyDeviceToHost, stream);
+        cudaStreamSynchronize(stream);
+        float t16 = 1e30f, t32 = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (!h_sat && timed_split(ctx, best.best, tour, n, dist, tmp[0], CVRPSD_I16, Ss, Ss, Q, L, stream_ptr,
+                                      &s_, &i_, &ms) == CVRPSD_OK && rep > 0)
+                t16 = std::min(t16, ms);
+            if (timed_split(ctx, best.best, tour, n, dist, tmp[1], CVRPSD_I32, Ss, Ss, Q, L, stream_ptr, &s_, &i_,
+                            &ms) == CVRPSD_OK && rep > 0)
+                t32 = std::min(t32, ms);
+        }
+        best.best_dtype = (!h_sat && t16 <= t32) ? CVRPSD_I16 : CVRPSD_I32;
+    } else {
+        cudaGetLastError();
+    }
+    for (void *p : tmp)
+        if (p) cudaFree(p);
+    if (sat) cudaFree(sat);
+
+    ctx->cfg = best.best;
+    ctx->profiling = saved_prof;
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"ms\": %.6f, "
+                       "\"dtype\": %d}\n",
+                    key.c_str(), best.best.threads, best.best.spt, best.best.ring, best.best_ms, best.best_dtype);
+            fclose(f);
+        }
+    }
+    *result = best;
+    return CVRPSD_OK;
+}
+
 struct cvrpsd_batch {
     cvrpsd_ctx *ctx = nullptr;
     int T = 0;

@@ -76,6 +76,40 @@ __global__ void __launch_bounds__(256) gen_demand_kernel(GenParams g, int rows_p
     }
 }
 
+template <typename TI, typename TO>
+__global__ void convert_demand_kernel(const TI *in, long long ld_in, TO *out, long long ld_out, int n, long long S,
+                                      unsigned int *saturated)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    for (int r = blockIdx.y; r < n; r += gridDim.y) {
+        const long long v = (long long)in[(long long)r * ld_in + s];
+        if (sizeof(TO) == 2 && (v > 32767 || v < -32768)) atomicOr(saturated, 1u);
+        out[(long long)r * ld_out + s] = (TO)(v > 32767 && sizeof(TO) == 2 ? 32767 : v);
+    }
+}
+
+cudaError_t launch_convert_demand(const void *in, int esize_in, long long ld_in, void *out, int esize_out,
+                                  long long ld_out, int n, long long S, unsigned int *saturated,
+                                  cudaStream_t stream)
+{
+    if (S == 0 || n == 0) return cudaSuccess;
+    dim3 grid((unsigned)((S + 255) / 256), (unsigned)(n < 64 ? n : 64));
+    if (esize_in == 2 && esize_out == 2)
+        convert_demand_kernel<int16_t, int16_t><<<grid, 256, 0, stream>>>((const int16_t *)in, ld_in, (int16_t *)out,
+                                                                          ld_out, n, S, saturated);
+    else if (esize_in == 2)
+        convert_demand_kernel<int16_t, int32_t><<<grid, 256, 0, stream>>>((const int16_t *)in, ld_in, (int32_t *)out,
+                                                                          ld_out, n, S, saturated);
+    else if (esize_out == 2)
+        convert_demand_kernel<int32_t, int16_t><<<grid, 256, 0, stream>>>((const int32_t *)in, ld_in, (int16_t *)out,
+                                                                          ld_out, n, S, saturated);
+    else
+        convert_demand_kernel<int32_t, int32_t><<<grid, 256, 0, stream>>>((const int32_t *)in, ld_in, (int32_t *)out,
+                                                                          ld_out, n, S, saturated);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gen_demand(const GenParams &g, int esize, cudaStream_t stream)
 {
     if (g.S == 0 || g.n == 0) return cudaSuccess;

@@ -107,6 +107,12 @@ cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeS
 cudaError_t launch_split_warp_batch(const BatchParams &b, int esize, int grid_ctas, int max_smem, bool configure_only,
                                     cudaStream_t stream);
 
+// Copy a [n][ld_in] demand matrix into a [n][ld_out] one of another element
+// type (first S columns); values outside int16 set *saturated (device flag).
+cudaError_t launch_convert_demand(const void *in, int esize_in, long long ld_in, void *out, int esize_out,
+                                  long long ld_out, int n, long long S, unsigned int *saturated,
+                                  cudaStream_t stream);
+
 // Scenario generator.
 struct GenParams {
     uint64_t seed;

@@ -259,3 +259,26 @@ def test_device_generator_matches_host_recipe(sp, cv, kind, dtype):
     # can only move a value across a rounding boundary: rare, and by 1
     assert np.abs(diff).max() <= 1
     assert (diff != 0).mean() < 1e-5
+
+
+# ------------------------------------------------------------ autotuner
+
+def test_autotune_picks_and_caches(sp, cv, tmp_path):
+    import json
+    w = workload("corr-n200", S=20_000)
+    inst = w.instances[0]
+    D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 20_000, dtype=np.int16)
+    dD = to_dev(D)
+    cache = tmp_path / "tune.jsonl"
+    r1 = sp.autotune(inst.tour, inst.dist, dD, inst.Q, inst.L, cache_path=cache)
+    assert r1["shapes_timed"] >= 12 and r1["ms"] > 0
+    assert r1["dtype"] in (cv.I16, cv.I32)
+    cfg = cv.cvrpsd_get_config(sp.ctx)
+    assert (cfg["threads"], cfg["spt"], cfg["ring"]) == (r1["threads"], r1["spt"], r1["ring"])
+    check_parity(sp, inst, D)                      # the tuned shape is still exact
+    lines = [json.loads(l) for l in open(cache)]
+    assert len(lines) == 1 and lines[0]["threads"] == r1["threads"]
+    sp.configure(kernel=0)
+    r2 = sp.autotune(inst.tour, inst.dist, dD, inst.Q, inst.L, cache_path=cache)
+    assert r2["shapes_timed"] == 0
+    assert (r2["threads"], r2["spt"], r2["ring"]) == (r1["threads"], r1["spt"], r1["ring"])
