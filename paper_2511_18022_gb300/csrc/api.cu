@@ -14,6 +14,7 @@
 
 #include "../../include/cvrpsd.h"
 #include "kernels.h"
+#include "tour_table.h"
 
 using namespace cvrpsd;
 
@@ -132,61 +133,13 @@ int ensure_scratch(cvrpsd_ctx *ctx, long long S)
     return CVRPSD_OK;
 }
 
-uint32_t key_scale(int n)
+// Table of one tour (see tour_table.h), with the message kept on the context.
+int build_tour_table(cvrpsd_ctx *ctx, const int32_t *tour, int n, const int32_t *dist, int Q, TourStep *tab,
+                     int32_t *g0)
 {
-    uint32_t K = 1;
-    while (K <= (uint32_t)n) K <<= 1;
-    return K;
-}
-
-// Validates the tour and distances and fills tab[0..n): row of sigma_i and
-//   C_i = c(sigma_i, 0) + c(0, sigma_{i+1}) - c(sigma_i, sigma_{i+1})   (i < n)
-//   C_n = D[n] + c(sigma_n, 0),  D[n] = sum_{t<n} c(sigma_t, sigma_{t+1}),
-// with g0 = c(0, sigma_1). Checks that every value the kernels form fits int32.
-int build_tour_table(cvrpsd_ctx *ctx, const int32_t *tour, int n, const int32_t *dist, int Q,
-                     TourStep *tab, int32_t *g0)
-{
-    if (!tour || !dist) return fail(ctx, CVRPSD_ERR_ARG, "tour and dist are required");
-    const long long N1 = (long long)n + 1;
-    std::vector<unsigned char> seen((size_t)n + 1, 0);
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        if (c < 1 || c > n) return fail(ctx, CVRPSD_ERR_ARG, "tour[%d] = %d is not a customer id in 1..%d", k, c, n);
-        if (seen[c]) return fail(ctx, CVRPSD_ERR_ARG, "customer %d appears twice in the tour", c);
-        seen[c] = 1;
-    }
-    long long singles = 0, Dn = 0, maxc = 0;
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        const long long out0 = dist[c], back = dist[(long long)c * N1];
-        const long long nxt = k + 1 < n ? dist[(long long)c * N1 + tour[k + 1]] : 0;
-        if (out0 < 0 || back < 0 || nxt < 0)
-            return fail(ctx, CVRPSD_ERR_ARG, "negative distance at tour position %d", k + 1);
-        singles += out0 + back;
-        Dn += nxt;
-        if (out0 > maxc) maxc = out0;
-        if (back > maxc) maxc = back;
-        if (nxt > maxc) maxc = nxt;
-    }
-    // |g| <= singles + D[n] + max c; every intermediate is bounded by that sum.
-    if (singles + Dn + 3 * maxc >= (1LL << 30))
-        return fail(ctx, CVRPSD_ERR_OVERFLOW, "route costs up to %lld do not fit the int32 arithmetic",
-                    singles + Dn + 3 * maxc);
-    const long long K = key_scale(n);
-    if ((long long)(Q + 1LL) * K + n >= (1LL << 31))
-        return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "Q = %d too large for n = %d (need (Q+1)*%lld + n < 2^31)", Q, n, K);
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        tab[k].row = c - 1;
-        if (k + 1 < n) {
-            const int d = tour[k + 1];
-            tab[k].c = (int32_t)(dist[(long long)c * N1] + dist[d] - dist[(long long)c * N1 + d]);
-        } else {
-            tab[k].c = (int32_t)(Dn + dist[(long long)c * N1]);
-        }
-    }
-    *g0 = dist[tour[0]];
-    return CVRPSD_OK;
+    char msg[256] = {0};
+    const int rc = fill_tour_table(tour, n, dist, Q, tab, g0, msg, sizeof(msg));
+    return rc ? fail(ctx, rc, "%s", msg) : CVRPSD_OK;
 }
 
 bool valid_shape(int threads, int spt, int ring)

@@ -23,6 +23,7 @@
 
 #include "../../include/cvrpsd.h"
 #include "kernels.h"
+#include "tour_table.h"
 
 namespace {
 
@@ -92,44 +93,6 @@ bool device_buffer_ok(const void *ptr, unsigned long long bytes, int device)
     return true;
 }
 
-// Same table and bounds as the context path: row of sigma_i and C_i, g0.
-int fill_table(const int32_t *tour, int n, const int32_t *dist, int Q, TourStep *tab, int32_t *g0)
-{
-    const long long N1 = (long long)n + 1;
-    static thread_local unsigned char seen[CVRPSD_MAX_N + 1];
-    for (int k = 0; k <= n; ++k) seen[k] = 0;
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        if (c < 1 || c > n || seen[c]) return CVRPSD_ERR_ARG;
-        seen[c] = 1;
-    }
-    long long singles = 0, Dn = 0, maxc = 0;
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        const long long out0 = dist[c], back = dist[(long long)c * N1];
-        const long long nxt = k + 1 < n ? dist[(long long)c * N1 + tour[k + 1]] : 0;
-        if (out0 < 0 || back < 0 || nxt < 0) return CVRPSD_ERR_ARG;
-        singles += out0 + back;
-        Dn += nxt;
-        maxc = out0 > maxc ? out0 : maxc;
-        maxc = back > maxc ? back : maxc;
-        maxc = nxt > maxc ? nxt : maxc;
-    }
-    if (singles + Dn + 3 * maxc >= (1LL << 30)) return CVRPSD_ERR_OVERFLOW;
-    uint32_t K = 1;
-    while (K <= (uint32_t)n) K <<= 1;
-    if ((long long)(Q + 1LL) * K + n >= (1LL << 31)) return CVRPSD_ERR_UNSUPPORTED;
-    for (int k = 0; k < n; ++k) {
-        const int c = tour[k];
-        tab[k].row = c - 1;
-        tab[k].c = k + 1 < n ? (int32_t)(dist[(long long)c * N1] + dist[tour[k + 1]] -
-                                         dist[(long long)c * N1 + tour[k + 1]])
-                             : (int32_t)(Dn + dist[(long long)c * N1]);
-    }
-    *g0 = dist[tour[0]];
-    return CVRPSD_OK;
-}
-
 }  // namespace
 
 extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
@@ -175,7 +138,8 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
     int32_t g0 = 0;
     {
         std::lock_guard<std::mutex> lock(g_host_mutex);
-        const int rc = fill_table(tour, n, dist, Q, g_host_tab, &g0);
+        char msg[256];
+        const int rc = fill_tour_table(tour, n, dist, Q, g_host_tab, &g0, msg, sizeof(msg));
         if (rc) return rc;
         // From pageable host memory: the copy has read the table when this returns.
         if (cudaMemcpyAsync(tab, g_host_tab, (size_t)n * sizeof(TourStep), cudaMemcpyHostToDevice, stream) !=
@@ -200,9 +164,7 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
         p.Q = Q;
         p.L = L;
         p.g0 = g0;
-        uint32_t K = 1;
-        while (K <= (uint32_t)n) K <<= 1;
-        p.K = K;
+        p.K = key_scale(n);
         p.out_cost = out_cost;
         p.acc = acc;
         p.ovf_list = list;

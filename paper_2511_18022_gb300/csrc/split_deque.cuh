@@ -32,13 +32,9 @@
 #include <stdint.h>
 
 #include "kernels.h"
+#include "tour_table.h"
 
 namespace cvrpsd {
-
-#ifndef CVRPSD_PREFETCH
-#define CVRPSD_PREFETCH 8
-#endif
-constexpr int kPrefetch = CVRPSD_PREFETCH;   // tour positions per prefetch block
 
 template <typename DT, int SPT> struct DemandVec;
 template <> struct DemandVec<int16_t, 1> { using T = short; };
@@ -114,18 +110,23 @@ struct Ring {
 // iteration (loads included) and applies it only if it still has an entry to
 // drop, so the warp never splits on this data-dependent control flow; the
 // loop ends when no lane has anything left (vote). Each scenario's walk is
-// exactly the sequential deque walk. With C_i > 0 (the usual case; C_i is
-// the same for all scenarios, so the test is uniform) the new value
-// min + C_i exceeds the front and the back pops cannot empty the deque.
-template <int R, int T, bool LCAP, bool PUSH>
+// exactly the sequential deque walk.
+//
+// The walk uses min(q, Q) for the load: a scenario with a larger (or a
+// negative) demand is flagged by qmax and re-evaluated elsewhere, and with
+// the clamp the back entry (candidate i-1) is always in the window, so the
+// front walk stops there at the latest. GENERAL: some C_i <= 0 in this block
+// (the host marks such blocks); only then can the new value min + C_i
+// undercut the front, so that back pops may empty the deque.
+template <int R, int T, bool LCAP, bool PUSH, bool GENERAL>
 __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, int ci, uint32_t K,
-                                       uint32_t xi, int L)
+                                       uint32_t xi, int L, int Q)
 {
     using RG = Ring<R, T>;
     d.qmax = max(d.qmax, (uint32_t)q);
-    d.pk += (uint32_t)q * K;
-    // front: drop entries that left the window (never past the back entry)
-    bool pf = (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe))) & (d.hoff != d.boff);
+    d.pk += (uint32_t)min(q, Q) * K;
+    // front: drop entries that left the window
+    bool pf = ((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe));
     while (__any_sync(0xffffffffu, pf)) {
         const uint32_t nh = RG::next(d.hoff);
         const int2 e = lds2(ring + nh);
@@ -133,13 +134,13 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
         d.fg = pf ? e.x : d.fg;
         d.fx = pf ? (uint32_t)e.y : d.fx;
         if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
-        pf = pf & (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe))) & (d.hoff != d.boff);
+        pf = pf & (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe)));
     }
     const int gi = d.fg + ci;
     if (!PUSH) return gi;
     const uint32_t x = d.pk + xi;               // K * (P(i) + Q) + i
     bool pb = d.bg >= gi;
-    if (ci > 0) {
+    if (!GENERAL) {
         // back: drop entries not smaller than gi (the front is smaller)
         while (__any_sync(0xffffffffu, pb)) {
             const uint32_t bp = RG::prev(d.boff);
@@ -210,13 +211,11 @@ __device__ __forceinline__ void block_accumulate(long long sum, unsigned inf, un
 
 // Positions of one prefetch block. GUARD: the block may run past n; the last
 // position reads f(n) instead of pushing. `tab` is the shared address of the
-// tour table (TourStep = {row, c}).
-// Positions of one prefetch block. GUARD: the block may run past n; the last
-// position reads f(n) instead of pushing. `tab` is the shared address of the
-// tour table (TourStep = {row, c}).
-template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD>
-__device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
-                                           uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L,
+// tour table (TourStep = {row, c}); the block's first row carries the
+// host's flag for a C_i <= 0 inside the block.
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool GENERAL>
+__device__ __forceinline__ void walk_steps(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
+                                           uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
                                            int (&out)[SPT])
 {
     const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u + 4u;
@@ -228,10 +227,21 @@ __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&rin
         const uint32_t xi = QK + (uint32_t)i;
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
-            if (!GUARD || i < n) dq_step<R, T, LCAP, true>(d[j], ring[j], q[u][j], i, ci, K, xi, L);
-            else out[j] = dq_step<R, T, LCAP, false>(d[j], ring[j], q[u][j], i, ci, K, xi, L);
+            if (!GUARD || i < n) dq_step<R, T, LCAP, true, GENERAL>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q);
+            else out[j] = dq_step<R, T, LCAP, false, GENERAL>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q);
         }
     }
+}
+
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD>
+__device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
+                                           uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
+                                           int (&out)[SPT])
+{
+    if (lds1(tab + (uint32_t)(i0 - 1) * 8u) & kRowFlagNonPositive)
+        walk_steps<DT, SPT, R, T, LCAP, GUARD, true>(d, ring, q, tab, i0, n, K, QK, L, Q, out);
+    else
+        walk_steps<DT, SPT, R, T, LCAP, GUARD, false>(d, ring, q, tab, i0, n, K, QK, L, Q, out);
 }
 
 // Demands of positions i0 .. i0 + kPrefetch - 1. Positions past n re-read row
@@ -243,7 +253,7 @@ __device__ __forceinline__ void prefetch_block(const char *base, uint32_t tab, i
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = CLAMP ? min(i0 + u, n) : i0 + u;
-        load_demands<DT, SPT>(base, lds1(tab + (uint32_t)(i - 1) * 8u), ldb, full, nvalid, q[u]);
+        load_demands<DT, SPT>(base, lds1(tab + (uint32_t)(i - 1) * 8u) & kRowMask, ldb, full, nvalid, q[u]);
     }
 }
 
@@ -290,17 +300,17 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     // below n: no guards or clamps.
     for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
         prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, out);
+        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, Q, out);
         prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out);
     }
     // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
     for (; i0 <= n; i0 += 2 * kPrefetch) {
         prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, out);
+        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, Q, out);
         if (i0 + kPrefetch > n) break;
         prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, out);
+        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out);
     }
 
     long long sum = 0;

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "kernels.h"
+#include "tour_table.h"
 
 namespace cvrpsd {
 
@@ -32,7 +33,7 @@ __device__ WarpResult warp_split_scenario(const TourStep *tab, int n, int Q, int
     // Demands in tour order, clamped to Q+1 (anything above Q is infeasible).
     bool neg = false, bad = false;
     for (int i = 1 + lane; i <= n; i += 32) {
-        int q = (int)dem[(long long)tab[i - 1].row * ld + s];
+        int q = (int)dem[(long long)(tab[i - 1].row & kRowMask) * ld + s];
         if (q < 0) { neg = true; q = 0; }
         if (q > Q) { bad = true; q = Q + 1; }
         P[i] = q;

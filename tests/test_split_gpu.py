@@ -282,3 +282,17 @@ def test_autotune_picks_and_caches(sp, cv, tmp_path):
     r2 = sp.autotune(inst.tour, inst.dist, dD, inst.Q, inst.L, cache_path=cache)
     assert r2["shapes_timed"] == 0
     assert (r2["threads"], r2["spt"], r2["ring"]) == (r1["threads"], r1["spt"], r1["ring"])
+
+
+def test_zero_break_costs_take_the_general_step(sp, cv):
+    """Customers alternate on both sides of the depot along one line, so the
+    depot lies on every tour edge and C_i = c(a,0) + c(0,b) - c(a,b) = 0:
+    every block is flagged and a new entry may empty the deque."""
+    n = 61
+    coords = [[0, 0]] + [[3 * k, 4 * k] if k % 2 else [-3 * k, -4 * k] for k in range(1, n + 1)]
+    inst = instance_from_coords(coords, list(range(1, n + 1)), Q=25, L=9)
+    rng = np.random.default_rng(11)
+    D = rng.integers(0, 7, size=(n, 2053)).astype(np.int16)
+    for shape in [(256, 1, 16), (128, 2, 32)]:
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+        check_parity(sp, inst, D)
