@@ -147,6 +147,23 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n,
                       int64_t *out_infeasible, double *out_mean, void *stream);
 
 /*
+ * cvrpsd_split_eval that also recovers the optimal routes (the Section 2
+ * Example lists a scenario's routes). For every scenario s and position
+ * i = 1..n, pred[(i-1) * ldp + s] (DEVICE int16, [n][ldp], ldp >= S) receives
+ * the p that attains f(i) in Eq. 1 -- the route ending at sigma_i starts at
+ * sigma_{p+1} -- taking the smallest such p on ties. The routes of scenario
+ * s follow by walking p = pred[n-1][s], pred[p-1][s], ... down to 0.
+ * Entries of infeasible scenarios are unspecified. Writing 2 bytes per
+ * (scenario, position) doubles the HBM traffic of the Split.
+ */
+int cvrpsd_split_routes(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n,
+                        const int32_t *dist, const void *demand,
+                        int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q,
+                        int32_t L, int32_t *out_cost, int16_t *pred, int64_t ldp,
+                        int64_t *out_sum, int64_t *out_infeasible,
+                        double *out_mean, void *stream);
+
+/*
  * Seeded scenario generator (workload synthesis, not part of the paper's
  * method). Writes demand[k-1][s] for customers k = 1..n and scenarios
  * s = 0..S-1 into the DEVICE [n][ld] matrix `out` of type `dtype`:

@@ -21,7 +21,7 @@ __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
     "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
-    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
 ]
@@ -196,6 +196,47 @@ def cvrpsd_gen_demand(ctx, seed: int, kind: int, mu, region, out, *, S: int | No
     _lib.check(ctx, rc)
 
 
+def cvrpsd_split_routes(ctx, tour, dist, demand, Q: int, L: int | None = None, *, pred, out_cost=None,
+                        S: int | None = None, stream=None) -> SplitResult:
+    """cvrpsd_split_eval plus the optimal predecessor of every (position,
+    scenario) in `pred`, a CUDA int16 tensor [n][ldp] (smallest p on ties)."""
+    tour = _i32(tour)
+    dist = _i32(dist)
+    n = int(tour.shape[0])
+    dptr, dcode, dshape = _dev(demand)
+    if dshape is None or len(dshape) != 2 or dshape[0] != n or dcode is None:
+        raise CvrpsdError(_lib.ERR_ARG, "demand must be a CUDA int16/int32 tensor [n][ld]")
+    import torch
+    if pred.dtype != torch.int16 or pred.dim() != 2 or pred.shape[0] != n or not pred.is_contiguous():
+        raise CvrpsdError(_lib.ERR_ARG, "pred must be a contiguous CUDA int16 tensor [n][ldp]")
+    pptr, _, _ = _dev(pred)
+    optr, _, _ = _dev(out_cost)
+    ld = dshape[1]
+    S = ld if S is None else S
+    s_sum, s_inf, s_mean = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    rc = _lib.load().cvrpsd_split_routes(ctx, tour.ctypes.data, n, dist.ctypes.data, dptr, int(dcode), int(S),
+                                         int(ld), int(Q), int(L or n), optr, pptr, int(pred.shape[1]),
+                                         ctypes.byref(s_sum), ctypes.byref(s_inf), ctypes.byref(s_mean),
+                                         _stream_ptr(stream))
+    _lib.check(ctx, rc)
+    return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)
+
+
+def routes_from_pred(tour, pred_column) -> list[list[int]]:
+    """Routes (lists of customer ids) of one scenario from its predecessor
+    column pred[:, s] (host array of n entries)."""
+    tour = np.asarray(tour)
+    ends, i = [], len(tour)
+    while i > 0:
+        ends.append(i)
+        i = int(pred_column[i - 1])
+    routes, start = [], 0
+    for e in reversed(ends):
+        routes.append([int(c) for c in tour[start:e]])
+        start = e
+    return routes
+
+
 def cvrpsd_autotune(ctx, tour, dist, demand, Q: int, L: int | None = None, *, S: int | None = None,
                     cache_path: str | None = None, stream=None) -> dict:
     """Time every launch shape on this workload, keep the fastest on the
@@ -345,6 +386,9 @@ class Splitter:
 
     def gen_demand(self, seed, kind, mu, region, out, **kw):
         cvrpsd_gen_demand(self.ctx, seed, kind, mu, region, out, **kw)
+
+    def split_routes(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
+        return cvrpsd_split_routes(self.ctx, tour, dist, demand, Q, L, **kw)
 
     def autotune(self, tour, dist, demand, Q, L=None, **kw) -> dict:
         return cvrpsd_autotune(self.ctx, tour, dist, demand, Q, L, **kw)

@@ -31,7 +31,7 @@ EXPORTS = [
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
     "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
-    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch", "cvrpsd_autotune",
+    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
 ]
 NOALLOC_MAX_S = 1048576
 
@@ -92,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_gen_demand.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, i32, i64, i64, i32, vp, vp]
     lib.cvrpsd_split_eval_noalloc.argtypes = [vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.cvrpsd_split_routes.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, i64, vp, vp,
+                                        vp, vp]
     lib.cvrpsd_autotune.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, ctypes.c_char_p,
                                     ctypes.POINTER(TuneResult), vp]
     lib.cvrpsd_batch_create.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, ctypes.POINTER(vp)]

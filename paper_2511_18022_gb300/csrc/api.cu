@@ -253,9 +253,14 @@ int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on)
     return CVRPSD_OK;
 }
 
-int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
-                      int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
-                      int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream_ptr)
+}  // extern "C"
+
+namespace {
+
+int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
+                    int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
+                    int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream_ptr, int16_t *pred,
+                    int64_t ldp)
 {
     if (!ctx) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
@@ -276,6 +281,11 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
         if (rc) return rc;
         if (out_cost) {
             rc = check_device_buffer(ctx, out_cost, (unsigned long long)S * 4, "out_cost");
+            if (rc) return rc;
+        }
+        if (pred) {
+            if (ldp < S) return fail(ctx, CVRPSD_ERR_ARG, "pred pitch %lld < S", (long long)ldp);
+            rc = check_device_buffer(ctx, pred, ((unsigned long long)(n - 1) * ldp + S) * 2, "pred");
             if (rc) return rc;
         }
     }
@@ -305,6 +315,8 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
     p.out_cost = out_cost;
     p.acc = ctx->d_acc;
     p.ovf_list = ctx->d_list;
+    p.pred = pred;
+    p.ldp = ldp;
 
     cvrpsd_stats st{};
     st.overflow = -1;
@@ -326,6 +338,8 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
         } else {
             DequeShape shape{256, 1, 16};
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
+            if (pred && (shape.spt != 1 || shape.threads == 64 || shape.ring == 64))
+                shape = DequeShape{256, 1, 16};      // route recovery shapes
             // Vector loads of spt demands need spt-aligned rows and base.
             while (shape.spt > 1 && (ld % shape.spt != 0 ||
                                      (uintptr_t)demand % ((uintptr_t)shape.spt * demand_dtype) != 0))
@@ -382,6 +396,29 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
     if (out_infeasible) *out_infeasible = inf;
     if (out_mean) *out_mean = (S - inf) > 0 ? (double)sum / (double)(S - inf) : NAN;
     return inf > 0 ? CVRPSD_WARN_INFEASIBLE : CVRPSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
+                      int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
+                      int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream)
+{
+    return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
+                           out_mean, stream, nullptr, 0);
+}
+
+int cvrpsd_split_routes(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
+                        int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
+                        int16_t *pred, int64_t ldp, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
+                        void *stream)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    if (!pred) return fail(ctx, CVRPSD_ERR_ARG, "pred is required");
+    return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
+                           out_mean, stream, pred, ldp);
 }
 
 }  // extern "C"

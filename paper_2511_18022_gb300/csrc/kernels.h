@@ -32,6 +32,8 @@ struct SplitParams {
     int32_t *out_cost;            // device [S] or nullptr
     unsigned long long *acc;      // device [ACC_WORDS]
     int32_t *ovf_list;            // device [S]: scenarios the deque could not hold
+    int16_t *pred;                // device [n][ldp] or nullptr: optimal predecessor of each position
+    long long ldp;
 };
 
 struct DequeShape {

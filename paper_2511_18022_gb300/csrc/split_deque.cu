@@ -5,10 +5,10 @@
 
 namespace cvrpsd {
 
-template <typename DT, int SPT, int R, int T, bool LCAP>
+template <typename DT, int SPT, int R, int T, bool LCAP, bool PRED = false>
 static cudaError_t launch_one(const SplitParams &p, const DequeShape &shape, cudaStream_t stream)
 {
-    auto kern = split_deque_kernel<DT, SPT, R, T, LCAP>;
+    auto kern = split_deque_kernel<DT, SPT, R, T, LCAP, PRED>;
     const size_t smem = split_deque_smem(p, shape);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -21,6 +21,12 @@ static cudaError_t launch_one(const SplitParams &p, const DequeShape &shape, cud
 template <typename DT, bool LCAP>
 static cudaError_t dispatch_shape(const SplitParams &p, const DequeShape &s, cudaStream_t st)
 {
+    if (p.pred) {   // route recovery: one scenario per thread
+        if (s.spt == 1 && s.threads == 128 && s.ring == 16) return launch_one<DT, 1, 16, 128, LCAP, true>(p, s, st);
+        if (s.spt == 1 && s.threads == 128 && s.ring == 32) return launch_one<DT, 1, 32, 128, LCAP, true>(p, s, st);
+        if (s.spt == 1 && s.threads == 256 && s.ring == 32) return launch_one<DT, 1, 32, 256, LCAP, true>(p, s, st);
+        return launch_one<DT, 1, 16, 256, LCAP, true>(p, DequeShape{256, 1, 16}, st);
+    }
 #define CVRPSD_CASE(T_, SPT_, R_) \
     if (s.threads == T_ && s.spt == SPT_ && s.ring == R_) return launch_one<DT, SPT_, R_, T_, LCAP>(p, s, st);
 #define CVRPSD_CASES_T(T_) \

@@ -118,9 +118,13 @@ struct Ring {
 // front walk stops there at the latest. GENERAL: some C_i <= 0 in this block
 // (the host marks such blocks); only then can the new value min + C_i
 // undercut the front, so that back pops may empty the deque.
-template <int R, int T, bool LCAP, bool PUSH, bool GENERAL>
+//
+// PRED: back entries are dropped only when strictly larger, so among equal
+// minima the oldest stays in front and the front is the smallest optimal
+// predecessor (the tie rule of route recovery).
+template <int R, int T, bool LCAP, bool PUSH, bool GENERAL, bool PRED = false>
 __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, int ci, uint32_t K,
-                                       uint32_t xi, int L, int Q)
+                                       uint32_t xi, int L, int Q, int *argmin = nullptr)
 {
     using RG = Ring<R, T>;
     d.qmax = max(d.qmax, (uint32_t)q);
@@ -137,9 +141,10 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
         pf = pf & (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe)));
     }
     const int gi = d.fg + ci;
+    if (PRED) *argmin = (int)(d.fx & (K - 1));   // the optimal predecessor, before the push
     if (!PUSH) return gi;
     const uint32_t x = d.pk + xi;               // K * (P(i) + Q) + i
-    bool pb = d.bg >= gi;
+    bool pb = PRED ? d.bg > gi : d.bg >= gi;
     if (!GENERAL) {
         // back: drop entries not smaller than gi (the front is smaller)
         while (__any_sync(0xffffffffu, pb)) {
@@ -147,7 +152,7 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
             const int below = lds1(ring + bp);
             d.boff = pb ? bp : d.boff;
             d.bg = pb ? below : d.bg;
-            pb = pb & (below >= gi);
+            pb = pb & (PRED ? below > gi : below >= gi);
         }
         d.boff = RG::next(d.boff);
     } else {
@@ -160,7 +165,7 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
             empty |= pb & emp;
             d.boff = pb ? bp : d.boff;
             d.bg = pb ? below : d.bg;
-            pb = pb & !emp & (below >= gi);
+            pb = pb & !emp & (PRED ? below > gi : below >= gi);
         }
         d.boff = RG::next(d.boff);
         d.hoff = empty ? d.boff : d.hoff;
@@ -213,10 +218,10 @@ __device__ __forceinline__ void block_accumulate(long long sum, unsigned inf, un
 // position reads f(n) instead of pushing. `tab` is the shared address of the
 // tour table (TourStep = {row, c}); the block's first row carries the
 // host's flag for a C_i <= 0 inside the block.
-template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool GENERAL>
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool GENERAL, bool PRED>
 __device__ __forceinline__ void walk_steps(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
                                            uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
-                                           int (&out)[SPT])
+                                           int (&out)[SPT], int16_t *pred, long long ldp)
 {
     const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u + 4u;
 #pragma unroll
@@ -227,21 +232,23 @@ __device__ __forceinline__ void walk_steps(Deque (&d)[SPT], const uint32_t (&rin
         const uint32_t xi = QK + (uint32_t)i;
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
-            if (!GUARD || i < n) dq_step<R, T, LCAP, true, GENERAL>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q);
-            else out[j] = dq_step<R, T, LCAP, false, GENERAL>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q);
+            int p = 0;
+            if (!GUARD || i < n) dq_step<R, T, LCAP, true, GENERAL, PRED>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q, &p);
+            else out[j] = dq_step<R, T, LCAP, false, GENERAL, PRED>(d[j], ring[j], q[u][j], i, ci, K, xi, L, Q, &p);
+            if (PRED && pred) pred[(long long)(i - 1) * ldp + j] = (int16_t)p;
         }
     }
 }
 
-template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD>
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool PRED>
 __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
                                            uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
-                                           int (&out)[SPT])
+                                           int (&out)[SPT], int16_t *pred, long long ldp)
 {
     if (lds1(tab + (uint32_t)(i0 - 1) * 8u) & kRowFlagNonPositive)
-        walk_steps<DT, SPT, R, T, LCAP, GUARD, true>(d, ring, q, tab, i0, n, K, QK, L, Q, out);
+        walk_steps<DT, SPT, R, T, LCAP, GUARD, true, PRED>(d, ring, q, tab, i0, n, K, QK, L, Q, out, pred, ldp);
     else
-        walk_steps<DT, SPT, R, T, LCAP, GUARD, false>(d, ring, q, tab, i0, n, K, QK, L, Q, out);
+        walk_steps<DT, SPT, R, T, LCAP, GUARD, false, PRED>(d, ring, q, tab, i0, n, K, QK, L, Q, out, pred, ldp);
 }
 
 // Demands of positions i0 .. i0 + kPrefetch - 1. Positions past n re-read row
@@ -263,10 +270,11 @@ __device__ __forceinline__ void prefetch_block(const char *base, uint32_t tab, i
 // given), returns the sum of those costs, and passes every scenario it sets
 // aside to `set_aside(s)`. Threads with no scenario (s_first >= S) walk
 // column 0 and report nothing: every lane must take part in the pop votes.
-template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside>
+template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside, bool PRED = false>
 __device__ __forceinline__ long long split_thread(const void *demand, long long ld, long long S, long long s_first,
                                                   int n, int Q, int L, uint32_t K, int g0, uint32_t rings,
-                                                  uint32_t tab, int tid, int32_t *out_cost, SetAside set_aside)
+                                                  uint32_t tab, int tid, int32_t *out_cost, SetAside set_aside,
+                                                  int16_t *pred_base = nullptr, long long ldp = 0)
 {
     using RG = Ring<R, T>;
     const long long rem = S - s_first;
@@ -275,6 +283,10 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     const uint32_t ldb = (uint32_t)(ld * (long long)sizeof(DT));
     const char *base = reinterpret_cast<const char *>(demand) + (nvalid ? s_first : 0) * (long long)sizeof(DT);
     const uint32_t QK = (uint32_t)Q * K;
+    // Route recovery runs with one scenario per thread; a thread without a
+    // scenario writes no predecessors.
+    static_assert(!PRED || SPT == 1, "predecessor output needs one scenario per thread");
+    int16_t *pred = PRED && nvalid ? pred_base + s_first : nullptr;
 
     Deque d[SPT];
     uint32_t ring[SPT];
@@ -300,17 +312,17 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     // below n: no guards or clamps.
     for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
         prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qa, tab, i0, n, K, QK, L, Q, out);
+        walk_block<DT, SPT, R, T, LCAP, false, PRED>(d, ring, qa, tab, i0, n, K, QK, L, Q, out, pred, ldp);
         prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-        walk_block<DT, SPT, R, T, LCAP, false>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out);
+        walk_block<DT, SPT, R, T, LCAP, false, PRED>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out, pred, ldp);
     }
     // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
     for (; i0 <= n; i0 += 2 * kPrefetch) {
         prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
-        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qa, tab, i0, n, K, QK, L, Q, out);
+        walk_block<DT, SPT, R, T, LCAP, true, PRED>(d, ring, qa, tab, i0, n, K, QK, L, Q, out, pred, ldp);
         if (i0 + kPrefetch > n) break;
         prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
-        walk_block<DT, SPT, R, T, LCAP, true>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out);
+        walk_block<DT, SPT, R, T, LCAP, true, PRED>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out, pred, ldp);
     }
 
     long long sum = 0;
@@ -330,7 +342,7 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     return sum;
 }
 
-template <typename DT, int SPT, int R, int T, bool LCAP>
+template <typename DT, int SPT, int R, int T, bool LCAP, bool PRED = false>
 __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -345,12 +357,13 @@ __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
     const long long s_first = ((long long)blockIdx.x * T + tid) * SPT;
     unsigned long long *acc = p.acc;
     int32_t *list = p.ovf_list;
-    const long long sum = split_thread<DT, SPT, R, T, LCAP>(
-        p.demand, p.ld, p.S, s_first, n, p.Q, p.L, p.K, p.g0, sbase, tab, tid, p.out_cost,
-        [acc, list](long long s) {
-            const unsigned long long idx = atomicAdd(acc + ACC_OVERFLOW, 1ull);
-            list[idx] = (int32_t)s;
-        });
+    auto set_aside = [acc, list](long long s) {
+        const unsigned long long idx = atomicAdd(acc + ACC_OVERFLOW, 1ull);
+        list[idx] = (int32_t)s;
+    };
+    const long long sum = split_thread<DT, SPT, R, T, LCAP, decltype(set_aside), PRED>(
+        p.demand, p.ld, p.S, s_first, n, p.Q, p.L, p.K, p.g0, sbase, tab, tid, p.out_cost, set_aside, p.pred,
+        p.ldp);
     block_accumulate(sum, 0u, 0u, p.acc);
 }
 

@@ -27,7 +27,8 @@ struct WarpResult {
 // this warp's shared arrays of n + 1 ints each.
 template <typename DT>
 __device__ WarpResult warp_split_scenario(const TourStep *tab, int n, int Q, int L, int g0, const DT *dem,
-                                          long long ld, long long s, int *P, int *g)
+                                          long long ld, long long s, int *P, int *g, int16_t *pred = nullptr,
+                                          long long ldp = 0)
 {
     const int lane = threadIdx.x & 31;
     // Demands in tour order, clamped to Q+1 (anything above Q is infeasible).
@@ -64,10 +65,17 @@ __device__ WarpResult warp_split_scenario(const TourStep *tab, int n, int Q, int
             const int Pi = P[i];
             if (i - lo > L) lo = i - L;
             while (Pi - P[lo] > Q) ++lo;            // same on every lane
-            int m = INT32_MAX;
-            for (int c = lo + lane; c < i; c += 32) m = min(m, g[c]);
-            m = __reduce_min_sync(0xffffffffu, m);
-            const int gi = tab[i - 1].c + m;
+            int m = INT32_MAX, at = INT32_MAX;
+            for (int c = lo + lane; c < i; c += 32) {
+                const int v = g[c];
+                if (v < m) { m = v; at = c; }          // first (smallest) c of this lane's minimum
+            }
+            const int mm = __reduce_min_sync(0xffffffffu, m);
+            const int gi = tab[i - 1].c + mm;
+            if (pred) {                                 // smallest optimal predecessor
+                const int p = __reduce_min_sync(0xffffffffu, m == mm ? at : INT32_MAX);
+                if (lane == 0) pred[(long long)(i - 1) * ldp + s] = (int16_t)p;
+            }
             if (lane == 0) g[i] = gi;
             __syncwarp();
         }
@@ -94,7 +102,7 @@ __global__ void __launch_bounds__(128) split_warp_kernel(SplitParams p, const in
     for (long long item = (long long)blockIdx.x * wpb + w; item < total;
          item += (long long)gridDim.x * wpb) {
         const long long s = list ? (long long)list[item] : item;
-        const WarpResult r = warp_split_scenario<DT>(p.tab, n, p.Q, p.L, p.g0, dem, p.ld, s, P, g);
+        const WarpResult r = warp_split_scenario<DT>(p.tab, n, p.Q, p.L, p.g0, dem, p.ld, s, P, g, p.pred, p.ldp);
         if (lane == 0) {
             if (r.neg) status |= ST_NEGATIVE_DEMAND;
             if (r.bad) ++inf; else sum += r.cost;
