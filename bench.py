@@ -421,6 +421,69 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate(args):
+    """surrogate-n200: label tours with the exact GPU Split, train the
+    surrogate on them, then compare surrogate-screened local search with
+    plain GPU-Split local search from the same start."""
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2511_18022_gb300 as cv
+    from paper_2511_18022_gb300 import build, search
+    from synth import workload
+
+    build.build()
+    w = workload("surrogate-n200", S=args.S or None)
+    inst, S = w.instances[0], w.S
+    sp = cv.Splitter(local)
+    D = torch.empty((inst.n, S), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0] + rank, cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    cust = search.customer_features(inst, D[:, :8192].cpu().numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tours, costs = search.training_set(sp.ctx, inst, D, args.train_pairs, seed=11)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    sur = cv.Surrogate(sp.ctx, cust, inst.dist, Q=float(inst.Q), seed=5)
+    t0 = time.perf_counter()
+    scale, mae = search.train_surrogate(sur, tours, costs, dist=inst.dist, epochs=args.epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    start = np.random.default_rng(1234).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    plain = search.LocalSearch(sp.ctx, inst, D, start, k=64, seed=99)
+    for _ in range(args.warmup):
+        plain.step()
+    plain = search.LocalSearch(sp.ctx, inst, D, start, k=64, seed=99)
+    plog = plain.run(args.steps)
+    screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=4096, k=64, seed=99,
+                                  retrain_every=25, scale=scale)
+    slog = screened.run(args.steps)
+    gap = (screened.cur_cost - plain.cur_cost) / plain.cur_cost
+    if rank == 0:
+        print(json.dumps({
+            "metric": "surrogate-screened local search: candidate tours/s (exact Split on the top 64 of 4096)",
+            "value": slog.candidates_per_s, "unit": "tours/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": slog.seconds / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, fp32 accumulation; i32 Split",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": inst.n, "S": S, "Q": inst.Q, "L": inst.L,
+                       "train_pairs": args.train_pairs, "epochs": args.epochs, "screen": 4096, "exact": 64},
+            "plain": {"candidate_tours_per_s": plog.candidates_per_s, "final_saa_cost": plain.cur_cost,
+                      "ms_per_iteration": plog.seconds / args.steps * 1e3},
+            "surrogate": {"candidate_tours_per_s": slog.candidates_per_s, "final_saa_cost": screened.cur_cost,
+                          "holdout_mae": mae, "cost_sd": float(costs.std().item()),
+                          "label_seconds": t_label, "train_seconds": t_train},
+            "speedup_candidates": slog.candidates_per_s / plog.candidates_per_s,
+            "final_cost_gap": gap,
+            "gpu_launches": None,
+        }))
+    sur.close()
+    sp.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,6 +502,8 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=8192)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default shape)")
+    ap.add_argument("--train-pairs", type=int, default=200_000, help="surrogate-n200: labelled tours")
+    ap.add_argument("--epochs", type=int, default=8, help="surrogate-n200: training epochs")
     args = ap.parse_args()
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
@@ -446,6 +511,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched-512":
         return run_batched(args)
+    if args.workload == "surrogate-n200":
+        return run_surrogate(args)
     return run_ours(args)
 
 

@@ -257,6 +257,80 @@ int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *
                             int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible,
                             double *out_mean, int32_t *out_status, void *stream);
 
+/* ---- Local search around the Split, on device-resident candidate tours ----
+ *
+ * The paper embeds the Split in a metaheuristic that evaluates many candidate
+ * giant tours of one instance (Section 1; the fixed-budget search of Section
+ * 4.3). These entry points keep the candidates on the device: they build
+ * neighbours, split all of them under the scenario set, pick the best, and
+ * screen neighbours with a learned surrogate. All are asynchronous on
+ * `stream`; every pointer named d_* is DEVICE memory. */
+
+/* SAA evaluation of T tours of one instance: d_tours [T][n] (each a
+ * permutation of 1..n; other values are clamped into range and give
+ * meaningless results), dist HOST (n+1)^2, demand DEVICE [n][ld] shared by all
+ * tours. Writes per tour d_mean (double, NaN if no scenario is feasible),
+ * d_sum and d_infeasible (int64); any of them may be NULL. Same arithmetic
+ * and bit-exact results as cvrpsd_split_eval per tour. */
+int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, int32_t n,
+                            const int32_t *dist, const void *demand, int32_t demand_dtype,
+                            int64_t S, int64_t ld, int32_t Q, int32_t L, double *d_mean,
+                            int64_t *d_sum, int64_t *d_infeasible, void *stream);
+
+/* Neighbours of d_base [n] under M moves d_moves [M][3] = (type, a, b) with
+ * 0 <= a, b < n (values outside are clamped): type 0 reverses positions a..b
+ * (2-opt), type 1 moves the customer at position a so that it ends at
+ * position b (relocate). Writes d_out [M][n]. */
+int cvrpsd_neighbors(cvrpsd_ctx *ctx, const int32_t *d_base, int32_t n, const int32_t *d_moves,
+                     int32_t M, int32_t *d_out, void *stream);
+
+/* Indices of the k smallest of d_scores [M] (1 <= k <= M <= 16384),
+ * ascending, ties to the smaller index, NaN last. Writes d_idx [k]. */
+int cvrpsd_topk(cvrpsd_ctx *ctx, const float *d_scores, int32_t M, int32_t k, int32_t *d_idx,
+                void *stream);
+
+/* d_out[r] = d_tours[d_idx[r]] for R rows of n ints; d_tours has `rows`
+ * rows and indices outside 0..rows-1 are clamped. */
+int cvrpsd_gather_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t rows, int32_t n,
+                        const int32_t *d_idx, int32_t R, int32_t *d_out, void *stream);
+
+/* Surrogate of a tour's SAA cost for screening neighbours (not part of the
+ * paper's method). Per position k it sees (x, y, mean demand, demand sd,
+ * fractional part of the cumulative mean demand / Q) of the customer there;
+ * layer 1 (256 units, ReLU) runs per position and is mean-pooled, the tour's
+ * closed length joins (see cvrpsd_surrogate_set_scale), layer 2 (256, ReLU)
+ * and layer 3 (scalar) follow. BF16
+ * weights, FP32 accumulation, Adam on FP32 master weights. */
+typedef struct cvrpsd_surrogate cvrpsd_surrogate;
+#define CVRPSD_SURROGATE_PARAMS 67841
+
+/* cust: HOST [n][4] = (x, y, mean demand, demand sd) of customer k at k-1
+ * (coordinates on the 0..1000 scale); dist HOST (n+1)^2; Q > 0; 1 <= n <= 4096;
+ * parameters drawn from `seed`. */
+int cvrpsd_surrogate_create(cvrpsd_ctx *ctx, int32_t n, const float *cust, const int32_t *dist,
+                            float Q, uint64_t seed, cvrpsd_surrogate **sur);
+int cvrpsd_surrogate_destroy(cvrpsd_surrogate *sur);
+/* d_pred [T] = network output for d_tours [T][n]. */
+int cvrpsd_surrogate_predict(cvrpsd_surrogate *sur, const int32_t *d_tours, int32_t T, float *d_pred,
+                             void *stream);
+/* One Adam step (rate lr) on the mean squared error to d_target [T]; the
+ * batch loss goes to d_loss (device float) if not NULL. */
+int cvrpsd_surrogate_train_step(cvrpsd_surrogate *sur, const int32_t *d_tours, int32_t T,
+                                const float *d_target, float lr, float *d_loss, void *stream);
+/* Gradient of that loss w.r.t. all parameters, without updating them
+ * (synchronous): h_grad HOST [CVRPSD_SURROGATE_PARAMS], h_loss HOST or NULL. */
+int cvrpsd_surrogate_gradients(cvrpsd_surrogate *sur, const int32_t *d_tours, int32_t T,
+                               const float *d_target, float *h_grad, float *h_loss);
+/* The tour-length input becomes (closed tour length - len_mean) / len_sd
+ * (default len_mean = 0, len_sd = 500 n); set it from the training tours so
+ * that the small length differences between neighbours are visible. */
+int cvrpsd_surrogate_set_scale(cvrpsd_surrogate *sur, float len_mean, float len_sd);
+
+/* Read (h_get) and/or replace (h_set) the FP32 parameters (HOST arrays of
+ * CVRPSD_SURROGATE_PARAMS: W1 [256][5], b1 [256], W2 [256][257], b2 [256],
+ * w3 [256], b3); *count receives the size. Synchronous. */
+int cvrpsd_surrogate_params(cvrpsd_surrogate *sur, float *h_get, const float *h_set, int64_t *count);
+
 /* Largest S accepted by cvrpsd_split_eval_noalloc. */
 #define CVRPSD_NOALLOC_MAX_S 1048576
 

@@ -21,7 +21,8 @@ __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
     "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
-    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
+    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
 ]
@@ -257,6 +258,113 @@ def cvrpsd_autotune(ctx, tour, dist, demand, Q: int, L: int | None = None, *, S:
     _lib.check(ctx, rc)
     return {"threads": res.best.threads, "spt": res.best.spt, "ring": res.best.ring,
             "ms": res.best_ms, "dtype": res.best_dtype, "shapes_timed": res.shapes_timed}
+
+
+def _dptr(t, dtype=None, what="buffer"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise CvrpsdError(_lib.ERR_ARG, f"{what} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise CvrpsdError(_lib.ERR_ARG, f"{what} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def cvrpsd_split_eval_tours(ctx, tours, dist, demand, Q: int, L: int | None = None, *, S: int | None = None,
+                            mean=None, sums=None, infeasible=None, stream=None):
+    """SAA evaluation of many device tours [T][n] of one instance (async)."""
+    import torch
+    T, n = int(tours.shape[0]), int(tours.shape[1])
+    dptr, dcode, dshape = _dev(demand)
+    if dshape is None or dshape[0] != n or dcode is None:
+        raise CvrpsdError(_lib.ERR_ARG, "demand must be a CUDA int16/int32 tensor [n][ld]")
+    ld = dshape[1]
+    S = ld if S is None else S
+    dist = _i32(dist)
+    rc = _lib.load().cvrpsd_split_eval_tours(
+        ctx, _dptr(tours, torch.int32, "tours"), T, n, dist.ctypes.data, dptr, int(dcode), int(S), int(ld),
+        int(Q), int(L or n), None if mean is None else _dptr(mean, torch.float64, "mean"),
+        None if sums is None else _dptr(sums, torch.int64, "sums"),
+        None if infeasible is None else _dptr(infeasible, torch.int64, "infeasible"), _stream_ptr(stream))
+    _lib.check(ctx, rc)
+
+
+def cvrpsd_neighbors(ctx, base, moves, out, stream=None):
+    import torch
+    _lib.check(ctx, _lib.load().cvrpsd_neighbors(ctx, _dptr(base, torch.int32, "base"), int(base.shape[0]),
+                                                 _dptr(moves, torch.int32, "moves"), int(moves.shape[0]),
+                                                 _dptr(out, torch.int32, "out"), _stream_ptr(stream)))
+
+
+def cvrpsd_topk(ctx, scores, k: int, out, stream=None):
+    import torch
+    _lib.check(ctx, _lib.load().cvrpsd_topk(ctx, _dptr(scores, torch.float32, "scores"), int(scores.shape[0]),
+                                            int(k), _dptr(out, torch.int32, "idx"), _stream_ptr(stream)))
+
+
+def cvrpsd_gather_tours(ctx, tours, idx, out, stream=None):
+    import torch
+    _lib.check(ctx, _lib.load().cvrpsd_gather_tours(ctx, _dptr(tours, torch.int32, "tours"), int(tours.shape[0]),
+                                                    int(tours.shape[1]),
+                                                    _dptr(idx, torch.int32, "idx"), int(idx.shape[0]),
+                                                    _dptr(out, torch.int32, "out"), _stream_ptr(stream)))
+
+
+class Surrogate:
+    """The tour-cost surrogate (cvrpsd_surrogate_*): hand-written BF16
+    training and inference kernels with FP32 accumulation."""
+
+    def __init__(self, ctx, cust, dist, Q: float, seed: int = 0):
+        cust = np.ascontiguousarray(cust, dtype=np.float32)
+        dist = _i32(dist)
+        h = ctypes.c_void_p()
+        _lib.check(ctx, _lib.load().cvrpsd_surrogate_create(ctx, int(cust.shape[0]), cust.ctypes.data,
+                                                            dist.ctypes.data, float(Q), int(seed) & (2**64 - 1),
+                                                            ctypes.byref(h)))
+        self.ctx, self.handle, self.n = ctx, h, int(cust.shape[0])
+
+    def set_scale(self, len_mean: float, len_sd: float):
+        _lib.check(self.ctx, _lib.load().cvrpsd_surrogate_set_scale(self.handle, float(len_mean), float(len_sd)))
+
+    def predict(self, tours, out, stream=None):
+        import torch
+        _lib.check(self.ctx, _lib.load().cvrpsd_surrogate_predict(
+            self.handle, _dptr(tours, torch.int32, "tours"), int(tours.shape[0]),
+            _dptr(out, torch.float32, "pred"), _stream_ptr(stream)))
+
+    def train_step(self, tours, target, lr: float, loss=None, stream=None):
+        import torch
+        _lib.check(self.ctx, _lib.load().cvrpsd_surrogate_train_step(
+            self.handle, _dptr(tours, torch.int32, "tours"), int(tours.shape[0]),
+            _dptr(target, torch.float32, "target"), float(lr),
+            None if loss is None else _dptr(loss, torch.float32, "loss"), _stream_ptr(stream)))
+
+    def gradients(self, tours, target):
+        import torch
+        g = np.zeros(_lib.SURROGATE_PARAMS, np.float32)
+        loss = ctypes.c_float(0.0)
+        _lib.check(self.ctx, _lib.load().cvrpsd_surrogate_gradients(
+            self.handle, _dptr(tours, torch.int32, "tours"), int(tours.shape[0]),
+            _dptr(target, torch.float32, "target"), g.ctypes.data, ctypes.byref(loss)))
+        return g, loss.value
+
+    def params(self, new=None) -> np.ndarray:
+        p = np.zeros(_lib.SURROGATE_PARAMS, np.float32)
+        cnt = ctypes.c_int64(0)
+        src = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        _lib.check(self.ctx, _lib.load().cvrpsd_surrogate_params(
+            self.handle, p.ctypes.data, None if src is None else src.ctypes.data, ctypes.byref(cnt)))
+        return p
+
+    def close(self):
+        if self.handle is not None:
+            _lib.load().cvrpsd_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _tour_descs(tours, S):

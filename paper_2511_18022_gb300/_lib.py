@@ -32,7 +32,12 @@ EXPORTS = [
     "cvrpsd_split_eval", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
     "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
     "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
+    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
+    "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
+    "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params",
+    "cvrpsd_surrogate_set_scale",
 ]
+SURROGATE_PARAMS = 67841
 NOALLOC_MAX_S = 1048576
 
 
@@ -94,6 +99,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_split_eval_noalloc.argtypes = [vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_split_routes.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, i64, vp, vp,
                                         vp, vp]
+    lib.cvrpsd_split_eval_tours.argtypes = [vp, vp, i32, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp]
+    lib.cvrpsd_neighbors.argtypes = [vp, vp, i32, vp, i32, vp, vp]
+    lib.cvrpsd_topk.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.cvrpsd_gather_tours.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
+    lib.cvrpsd_surrogate_create.argtypes = [vp, i32, vp, vp, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.cvrpsd_surrogate_destroy.argtypes = [vp]
+    lib.cvrpsd_surrogate_predict.argtypes = [vp, vp, i32, vp, vp]
+    lib.cvrpsd_surrogate_train_step.argtypes = [vp, vp, i32, vp, ctypes.c_float, vp, vp]
+    lib.cvrpsd_surrogate_gradients.argtypes = [vp, vp, i32, vp, vp, vp]
+    lib.cvrpsd_surrogate_params.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+    lib.cvrpsd_surrogate_set_scale.argtypes = [vp, ctypes.c_float, ctypes.c_float]
     lib.cvrpsd_autotune.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, ctypes.c_char_p,
                                     ctypes.POINTER(TuneResult), vp]
     lib.cvrpsd_batch_create.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, ctypes.POINTER(vp)]

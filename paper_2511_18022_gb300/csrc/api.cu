@@ -13,49 +13,13 @@
 #include <vector>
 
 #include "../../include/cvrpsd.h"
+#include "ctx.h"
 #include "kernels.h"
 #include "tour_table.h"
 
 using namespace cvrpsd;
 
-struct cvrpsd_ctx {
-    int device = 0;
-    int sm_count = 0;
-    int max_smem = 48 * 1024;              // opt-in shared memory per block
-    unsigned long long *d_acc = nullptr;   // ACC_WORDS
-    int32_t *d_list = nullptr;             // overflow list
-    long long list_cap = 0;
-    TourStep *d_tab = nullptr;
-    TourStep *h_tab = nullptr;             // pinned
-    unsigned long long *h_acc = nullptr;   // pinned
-    int32_t *d_gen = nullptr;              // mu[n], region[n]
-    int32_t *h_gen = nullptr;              // pinned
-    cudaEvent_t ev_tab = nullptr;          // tab upload done
-    cudaEvent_t ev_gen = nullptr;          // gen upload done
-    cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};   // kernel timing (profiling)
-    int profiling = 0;
-    cvrpsd_config cfg{0, 0, 0, 0};
-    cvrpsd_stats stats{};
-    char err[512] = {0};
-};
-
 namespace {
-
-int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
-{
-    if (ctx) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
-        va_end(ap);
-    }
-    return code;
-}
-
-int cuda_fail(cvrpsd_ctx *ctx, cudaError_t e, const char *what)
-{
-    return fail(ctx, CVRPSD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
 #define CK(call, what)                                     \
     do {                                                   \
@@ -211,6 +175,11 @@ int cvrpsd_destroy(cvrpsd_ctx *ctx)
     if (ctx->ev_gen) cudaEventDestroy(ctx->ev_gen);
     for (cudaEvent_t e : ctx->ev_t)
         if (e) cudaEventDestroy(e);
+    if (ctx->mt_tabs) cudaFree(ctx->mt_tabs);
+    if (ctx->mt_descs) cudaFree(ctx->mt_descs);
+    if (ctx->mt_acc) cudaFree(ctx->mt_acc);
+    if (ctx->mt_list) cudaFree(ctx->mt_list);
+    if (ctx->mt_dist) cudaFree(ctx->mt_dist);
     delete ctx;
     return CVRPSD_OK;
 }
@@ -738,6 +707,7 @@ int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tour
     BatchParams &bp = b->bp;
     bp.tours = b->d_tours;
     bp.items = b->d_items;
+    bp.tiles = (int)tiles;
     bp.n_items = (int)items.size();
     bp.S = S;
     bp.acc = b->d_acc;

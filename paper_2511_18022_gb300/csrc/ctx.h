@@ -1,0 +1,65 @@
+// Internal: the library context and its error helpers (shared by the C ABI
+// translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "../../include/cvrpsd.h"
+#include "kernels.h"
+
+using cvrpsd::TourDev;
+using cvrpsd::TourStep;
+
+struct cvrpsd_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int max_smem = 48 * 1024;              // opt-in shared memory per block
+    unsigned long long *d_acc = nullptr;   // ACC_WORDS
+    int32_t *d_list = nullptr;             // overflow list
+    long long list_cap = 0;
+    TourStep *d_tab = nullptr;
+    TourStep *h_tab = nullptr;             // pinned
+    unsigned long long *h_acc = nullptr;   // pinned
+    int32_t *d_gen = nullptr;              // mu[n], region[n]
+    int32_t *h_gen = nullptr;              // pinned
+    cudaEvent_t ev_tab = nullptr;          // tab upload done
+    cudaEvent_t ev_gen = nullptr;          // gen upload done
+    cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};   // kernel timing (profiling)
+    int profiling = 0;
+    cvrpsd_config cfg{0, 0, 0, 0};
+    cvrpsd_stats stats{};
+    char err[512] = {0};
+    // many tours of one instance (cvrpsd_split_eval_tours), grown on demand
+    TourStep *mt_tabs = nullptr;
+    long long mt_tabs_cap = 0;
+    TourDev *mt_descs = nullptr;
+    int mt_descs_cap = 0;
+    unsigned long long *mt_acc = nullptr;
+    int mt_acc_cap = 0;
+    int2 *mt_list = nullptr;
+    long long mt_list_cap = 0;
+    int32_t *mt_dist = nullptr;
+    long long mt_dist_cap = 0;
+};
+
+namespace cvrpsd {
+
+inline int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+inline int cuda_fail(cvrpsd_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, CVRPSD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace cvrpsd

@@ -84,8 +84,10 @@ enum BatchStatusBits { BST_LIST_FULL = 1 };
 
 struct BatchParams {
     const TourDev *tours;         // device [T]
-    const int2 *items;            // device [n_items]: (tour, scenario tile), in processing order
+    const int2 *items;            // device [n_items]: (tour, scenario tile), in processing order;
+                                  // nullptr: item = tour * tiles + tile
     int n_items;
+    int tiles;                    // scenario tiles per tour (with items == nullptr)
     long long S;                  // scenarios per tour
     unsigned long long *acc;      // device [BACC_WORDS + 3 T]
     int2 *list;                   // device [list_cap]: set-aside (tour, scenario)
@@ -108,6 +110,17 @@ cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeS
                                    bool configure_only, int *blocks_per_sm, cudaStream_t stream);
 cudaError_t launch_split_warp_batch(const BatchParams &b, int esize, int grid_ctas, int max_smem, bool configure_only,
                                     cudaStream_t stream);
+
+// Local search on the device (search.cu).
+cudaError_t launch_neighbors(const int32_t *base, int n, const int32_t *moves, int M, int32_t *out, cudaStream_t st);
+cudaError_t launch_tour_tables(const int32_t *tours, int T, int n, const int32_t *dist, int32_t *D_out,
+                               TourStep *tabs, TourDev *descs, const void *demand, long long ld, int Q, int L,
+                               uint32_t K, cudaStream_t st);
+cudaError_t launch_tour_means(const unsigned long long *acc, int T, long long S, double *mean, long long *sum,
+                              long long *inf, cudaStream_t st);
+cudaError_t launch_topk(const float *scores, int M, int k, int32_t *idx_out, cudaStream_t st);
+cudaError_t launch_gather_rows(const int32_t *in, int rows, int n, const int32_t *idx, int R, int32_t *out,
+                               cudaStream_t st);
 
 // Copy a [n][ld_in] demand matrix into a [n][ld_out] one of another element
 // type (first S columns); values outside int16 set *saturated (device flag).

@@ -1,0 +1,358 @@
+// Surrogate network for screening local-search neighbours: training and
+// inference kernels. BF16 weights, FP32 activations and accumulation.
+//
+// Architecture (width H = 256):
+//   per position k of a tour:  phi_k = (x, y, mu / Q, sd / Q, frac(cum_k / Q))
+//                              (coordinates / 1000; cum_k = expected load of
+//                               positions 1..k along the tour)
+//   layer 1 (per position):    h_k = relu(W1 phi_k + b1)            H x 5
+//   pooling:                   z = mean_k h_k
+//   tour-length feature:       t = (c(0,s_1) + D[n] + c(s_n,0) - m) / sd, with (m, sd)
+//                              set by the caller (default m = 0, sd = 500 n)
+//   layer 2:                   u = relu(W2 [z; t] + b2)              H x (H+1)
+//   layer 3:                   y = w3 . u + b3
+// Parameters are one fp32 vector (layout in mlp.h); the kernels read bf16
+// copies of the weight matrices. The backward pass recomputes layer 1 from the
+// tour instead of storing an activation per position.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "mlp.h"
+
+namespace cvrpsd {
+
+// ---------------------------------------------------------------- layer 1
+
+// One block (H threads) per tour: features in shared memory, then thread j
+// accumulates relu(pre_kj) over the positions. TRAIN=false writes z and t;
+// BACKWARD=true instead reads dz and accumulates dW1 / db1.
+template <bool BACKWARD>
+__global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
+{
+    extern __shared__ float feat[];           // [n][5]
+    __shared__ float s_part[kMlpH / 32];
+    __shared__ float s_carry;
+    const int n = a.n, j = threadIdx.x, lane = j & 31, w = j >> 5;
+    const long long N1 = (long long)n + 1;
+    for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
+        const int32_t *tour = a.tours + (long long)t * n;
+        // features and the tour length
+        float len = 0.0f;
+        if (j == 0) s_carry = 0.0f;
+        __syncthreads();
+        for (int k0 = 0; k0 < n; k0 += kMlpH) {
+            const int k = k0 + j;
+            float m = 0.0f;
+            int c = 1;
+            if (k < n) {
+                c = min(max(tour[k], 1), n);
+                m = a.cust[(c - 1) * 4 + 2];
+                const int nx = k + 1 < n ? min(max(tour[k + 1], 1), n) : 0;
+                len += (float)a.dist[(long long)c * N1 + nx];
+                if (k == 0) len += (float)a.dist[c];
+            }
+            // inclusive scan of mu / Q over this chunk
+            float v = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (lane == 31) s_part[w] = v;
+            __syncthreads();
+            float off = s_carry;
+            for (int q = 0; q < w; ++q) off += s_part[q];
+            const float cum = off + v;
+            if (k < n) {
+                float *f = feat + 5 * k;
+                f[0] = a.cust[(c - 1) * 4 + 0];
+                f[1] = a.cust[(c - 1) * 4 + 1];
+                f[2] = m;
+                f[3] = a.cust[(c - 1) * 4 + 3];
+                f[4] = cum - floorf(cum);
+            }
+            __syncthreads();
+            if (j == kMlpH - 1) s_carry = cum;
+            __syncthreads();
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
+        if (lane == 0) s_part[w] = len;
+        __syncthreads();
+        float tl = 0.0f;
+        for (int q = 0; q < kMlpH / 32; ++q) tl += s_part[q];
+        tl = (tl - a.len_mean) * a.len_inv_sd;
+
+        float wj[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) wj[f] = __bfloat162float(a.w1[j * 5 + f]);
+        const float bj = __bfloat162float(a.b1[j]);
+        if (!BACKWARD) {
+            float acc = 0.0f;
+            for (int k = 0; k < n; ++k) {
+                const float *f = feat + 5 * k;
+                const float pre = bj + wj[0] * f[0] + wj[1] * f[1] + wj[2] * f[2] + wj[3] * f[3] + wj[4] * f[4];
+                acc += fmaxf(pre, 0.0f);
+            }
+            a.zt[(long long)t * kMlpIn2 + j] = acc / (float)n;
+            if (j == 0) a.zt[(long long)t * kMlpIn2 + kMlpH] = tl;
+        } else {
+            const float g = a.dzt[(long long)t * kMlpIn2 + j] / (float)n;
+            float gw[5] = {0, 0, 0, 0, 0}, gb = 0.0f;
+            if (g != 0.0f) {
+                for (int k = 0; k < n; ++k) {
+                    const float *f = feat + 5 * k;
+                    const float pre = bj + wj[0] * f[0] + wj[1] * f[1] + wj[2] * f[2] + wj[3] * f[3] + wj[4] * f[4];
+                    if (pre > 0.0f) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) gw[q] += f[q];
+                        gb += 1.0f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) atomicAdd(a.gw1 + j * 5 + q, g * gw[q]);
+            atomicAdd(a.gb1 + j, g * gb);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- GEMMs
+// 32 x 32 output tile per block of 256 threads (4 outputs per thread), the
+// reduction dimension in chunks of 32 through shared memory.
+
+// out[b][o] = act(sum_k X[b][k] W[o][k] + bias[o])      X fp32, W bf16
+__global__ void __launch_bounds__(256) gemm_xwt_kernel(const float *X, int B, int Kd, int ldx,
+                                                       const __nv_bfloat16 *W, int N, int ldw, const __nv_bfloat16 *bias,
+                                                       float *out, int ldo, int relu)
+{
+    __shared__ float sx[32][33], sw[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // ty 0..7
+    const int b0 = blockIdx.y * 32, o0 = blockIdx.x * 32;
+    float acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < Kd; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int b = b0 + r, o = o0 + r, k = k0 + tx;
+            sx[r][tx] = (b < B && k < Kd) ? X[(long long)b * ldx + k] : 0.0f;
+            sw[r][tx] = (o < N && k < Kd) ? __bfloat162float(W[(long long)o * ldw + k]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const float wv = sw[tx][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += sx[ty + 8 * q][k] * wv;
+        }
+        __syncthreads();
+    }
+    const int o = o0 + tx;
+    if (o >= N) return;
+    const float bo = bias ? __bfloat162float(bias[o]) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int b = b0 + ty + 8 * q;
+        if (b < B) {
+            float v = acc[q] + bo;
+            if (relu) v = fmaxf(v, 0.0f);
+            out[(long long)b * ldo + o] = v;
+        }
+    }
+}
+
+// out[b][k] = sum_o G[b][o] W[o][k]                     G fp32, W bf16 [N][ldw]
+__global__ void __launch_bounds__(256) gemm_gw_kernel(const float *G, int B, int N, int ldg, const __nv_bfloat16 *W,
+                                                      int Kd, int ldw, float *out, int ldo)
+{
+    __shared__ float sg[32][33], sw[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int b0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    float acc[4] = {0, 0, 0, 0};
+    for (int o0 = 0; o0 < N; o0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int b = b0 + r, o = o0 + tx;
+            sg[r][tx] = (b < B && o < N) ? G[(long long)b * ldg + o] : 0.0f;
+            const int oo = o0 + r, kk = k0 + tx;
+            sw[r][tx] = (oo < N && kk < Kd) ? __bfloat162float(W[(long long)oo * ldw + kk]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int o = 0; o < 32; ++o) {
+            const float wv = sw[o][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += sg[ty + 8 * q][o] * wv;
+        }
+        __syncthreads();
+    }
+    const int k = k0 + tx;
+    if (k >= Kd) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int b = b0 + ty + 8 * q;
+        if (b < B) out[(long long)b * ldo + k] = acc[q];
+    }
+}
+
+// out[o][k] += sum_b G[b][o] X[b][k]                    G, X fp32 (weight gradient)
+__global__ void __launch_bounds__(256) gemm_gtx_kernel(const float *G, int B, int N, int ldg, const float *X, int Kd,
+                                                       int ldx, float *out, int ldo)
+{
+    __shared__ float sg[32][33], sx[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    float acc[4] = {0, 0, 0, 0};
+    for (int b0 = 0; b0 < B; b0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int b = b0 + r;
+            sg[r][tx] = (b < B && o0 + tx < N) ? G[(long long)b * ldg + o0 + tx] : 0.0f;
+            sx[r][tx] = (b < B && k0 + tx < Kd) ? X[(long long)b * ldx + k0 + tx] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+            const float xv = sx[b][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += sg[b][ty + 8 * q] * xv;
+        }
+        __syncthreads();
+    }
+    const int k = k0 + tx;
+    if (k >= Kd) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = o0 + ty + 8 * q;
+        if (o < N) out[(long long)o * ldo + k] += acc[q];
+    }
+}
+
+// ---------------------------------------------------------------- layer 3, loss
+
+// y[b] = w3 . u_b + b3; with targets: dy = 2 (y - target) / B, loss partials.
+__global__ void mlp_out_kernel(const float *U, int B, const __nv_bfloat16 *w3, const __nv_bfloat16 *b3, float *y,
+                               const float *target, float *dy, float *loss)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    float s = 0.0f;
+    for (int j = lane; j < kMlpH; j += 32) s += U[(long long)b * kMlpH + j] * __bfloat162float(w3[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const float v = s + __bfloat162float(b3[0]);
+        y[b] = v;
+        if (target) {
+            const float e = v - target[b];
+            dy[b] = 2.0f * e / (float)B;
+            atomicAdd(loss, e * e / (float)B);
+        }
+    }
+}
+
+// dU[b][j] = dy_b w3_j [u_bj > 0]; g_w3[j] += sum_b dy_b u_bj; g_b3 += sum_b dy_b
+__global__ void mlp_out_backward_kernel(const float *U, int B, const float *dy, const __nv_bfloat16 *w3, float *dU,
+                                        float *gw3, float *gb3)
+{
+    const int j = threadIdx.x;                // kMlpH threads
+    float acc = 0.0f, accb = 0.0f;
+    const float wj = __bfloat162float(w3[j]);
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+        const float u = U[(long long)b * kMlpH + j];
+        const float d = dy[b];
+        acc += d * u;
+        accb += d;
+        dU[(long long)b * kMlpH + j] = u > 0.0f ? d * wj : 0.0f;
+    }
+    atomicAdd(gw3 + j, acc);
+    if (j == 0) atomicAdd(gb3, accb);
+}
+
+// g_b2[j] += sum_b dU[b][j]
+__global__ void colsum_kernel(const float *G, int B, int N, int ldg, float *out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s += G[(long long)b * ldg + j];
+    out[j] += s;
+}
+
+// ---------------------------------------------------------------- Adam
+
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, long long P, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *p, __nv_bfloat16 *q, long long P)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x)
+        q[i] = __float2bfloat16_rn(p[i]);
+}
+
+// ---------------------------------------------------------------- host launchers
+
+static dim3 grid2(int cols, int rows) { return dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)); }
+
+cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U, float *y, const float *target,
+                        float *dy, float *loss, cudaStream_t st)
+{
+    const int T = l1.T;
+    const size_t smem = (size_t)l1.n * 5 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(mlp_layer1_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    mlp_layer1_kernel<false><<<T < 16384 ? T : 16384, kMlpH, smem, st>>>(l1);
+    gemm_xwt_kernel<<<grid2(kMlpH, T), 256, 0, st>>>(l1.zt, T, kMlpIn2, kMlpIn2, wt.w2, kMlpH, kMlpIn2, wt.b2, U, kMlpH,
+                                                      1);
+    mlp_out_kernel<<<(T + 7) / 8, 256, 0, st>>>(U, T, wt.w3, wt.b3, y, target, dy, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const float *U, const float *dy, float *dU,
+                         float *dzt, float *grad, cudaStream_t st)
+{
+    const int T = l1.T;
+    float *gw1 = grad + kOffW1, *gb1 = grad + kOffB1, *gw2 = grad + kOffW2, *gb2 = grad + kOffB2;
+    float *gw3 = grad + kOffW3, *gb3 = grad + kOffB3;
+    mlp_out_backward_kernel<<<T < 512 ? T : 512, kMlpH, 0, st>>>(U, T, dy, wt.w3, dU, gw3, gb3);
+    gemm_gtx_kernel<<<grid2(kMlpIn2, kMlpH), 256, 0, st>>>(dU, T, kMlpH, kMlpH, l1.zt, kMlpIn2, kMlpIn2, gw2, kMlpIn2);
+    colsum_kernel<<<1, kMlpH, 0, st>>>(dU, T, kMlpH, kMlpH, gb2);
+    gemm_gw_kernel<<<grid2(kMlpIn2, T), 256, 0, st>>>(dU, T, kMlpH, kMlpH, wt.w2, kMlpIn2, kMlpIn2, dzt, kMlpIn2);
+    MlpLayer1Args b = l1;
+    b.dzt = dzt;
+    b.gw1 = gw1;
+    b.gb1 = gb1;
+    const size_t smem = (size_t)l1.n * 5 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(mlp_layer1_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    mlp_layer1_kernel<true><<<T < 16384 ? T : 16384, kMlpH, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, float lr, int step,
+                     cudaStream_t st)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    adam_kernel<<<128, 256, 0, st>>>(p, g, m, v, kMlpParams, lr, b1, b2, eps, c1, c2);
+    to_bf16_kernel<<<128, 256, 0, st>>>(p, pb, kMlpParams);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_to_bf16(const float *p, __nv_bfloat16 *pb, cudaStream_t st)
+{
+    to_bf16_kernel<<<128, 256, 0, st>>>(p, pb, kMlpParams);
+    return cudaGetLastError();
+}
+
+}  // namespace cvrpsd

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
         __syncthreads();
         const int item = s_item;
         if (item >= b.n_items) break;
-        const int2 it = b.items[item];
+        const int2 it = b.items ? b.items[item] : make_int2(item / b.tiles, item % b.tiles);
         const TourDev td = b.tours[it.x];
         if (it.x != cur) {
             for (int k = tid; k < td.n; k += T) tabp[k] = td.tab[k];

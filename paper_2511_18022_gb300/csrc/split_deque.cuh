@@ -129,8 +129,11 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
     using RG = Ring<R, T>;
     d.qmax = max(d.qmax, (uint32_t)q);
     d.pk += (uint32_t)min(q, Q) * K;
-    // front: drop entries that left the window
-    bool pf = ((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe));
+    // front: drop entries that left the window. A scenario whose ring has
+    // overflowed is frozen (no more pops): its ring no longer holds a valid
+    // deque, and the warp kernel recomputes it anyway; this keeps every pop
+    // loop bounded.
+    bool pf = (((int)(d.fx - d.pk) < 0) | (LCAP & (i >= d.fe))) & !d.ovf;
     while (__any_sync(0xffffffffu, pf)) {
         const uint32_t nh = RG::next(d.hoff);
         const int2 e = lds2(ring + nh);
@@ -144,7 +147,7 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
     if (PRED) *argmin = (int)(d.fx & (K - 1));   // the optimal predecessor, before the push
     if (!PUSH) return gi;
     const uint32_t x = d.pk + xi;               // K * (P(i) + Q) + i
-    bool pb = PRED ? d.bg > gi : d.bg >= gi;
+    bool pb = (PRED ? d.bg > gi : d.bg >= gi) & !d.ovf;
     if (!GENERAL) {
         // back: drop entries not smaller than gi (the front is smaller)
         while (__any_sync(0xffffffffu, pb)) {

@@ -1,0 +1,208 @@
+"""Local search over giant tours with the exact GPU Split as the judge and an
+optional learned surrogate that screens neighbours.
+
+Each iteration draws random 2-opt / relocate moves of the current tour
+(seeded host RNG), and the library's kernels do the rest on the device:
+
+* build the neighbour tours;
+* screen them with the surrogate and keep the k best scores, or, without a
+  surrogate, keep k random neighbours;
+* evaluate those k tours exactly under every scenario;
+* accept the best one if it improves the current SAA cost.
+
+The exact Split stays the arbiter: the surrogate only decides which
+neighbours get evaluated. This module sequences calls and holds no arithmetic
+of the Split or of the network.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (Surrogate, cvrpsd_gather_tours, cvrpsd_neighbors, cvrpsd_split_eval_tours, cvrpsd_topk)
+
+
+def random_moves(rng: np.random.Generator, M: int, n: int) -> np.ndarray:
+    """M moves (type, a, b): half 2-opt segment reversals, half relocations."""
+    t = rng.integers(0, 2, M)
+    a = rng.integers(0, n, M)
+    b = rng.integers(0, n - 1, M)
+    b = b + (b >= a)                      # b != a
+    return np.stack([t, a, b], axis=1).astype(np.int32)
+
+
+def customer_features(inst, D_host_sample: np.ndarray) -> np.ndarray:
+    """(x, y, mean demand, demand sd) per customer, from a sample of scenario
+    columns [n][s] (the statistics the surrogate sees)."""
+    d = D_host_sample.astype(np.float64)
+    return np.column_stack([inst.coords[1:, 0], inst.coords[1:, 1], d.mean(axis=1),
+                            d.std(axis=1)]).astype(np.float32)
+
+
+class Evaluator:
+    """Exact SAA costs of device tours of one instance."""
+
+    def __init__(self, ctx, inst, D):
+        import torch
+        self.ctx, self.inst, self.D = ctx, inst, D
+        self._mean = torch.empty(0, dtype=torch.float64, device=D.device)
+
+    def __call__(self, tours):
+        import torch
+        T = int(tours.shape[0])
+        if self._mean.numel() < T:
+            self._mean = torch.empty(T, dtype=torch.float64, device=tours.device)
+        out = self._mean[:T]
+        cvrpsd_split_eval_tours(self.ctx, tours, self.inst.dist, self.D, self.inst.Q, self.inst.L, mean=out)
+        return out
+
+
+@dataclass
+class SearchLog:
+    costs: list = field(default_factory=list)     # current SAA cost after each iteration
+    screened: int = 0                             # candidate tours considered
+    evaluated: int = 0                            # tours split exactly
+    seconds: float = 0.0
+
+    @property
+    def candidates_per_s(self) -> float:
+        return self.screened / self.seconds if self.seconds else 0.0
+
+
+class LocalSearch:
+    """Best-improvement local search from `start` (host int array of ids)."""
+
+    def __init__(self, ctx, inst, D, start, *, surrogate: Surrogate | None = None, M: int = 4096, k: int = 64,
+                 seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4):
+        import torch
+        self.ctx, self.inst, self.D = ctx, inst, D
+        self.n = inst.n
+        self.M, self.k = (M if surrogate is not None else k), k
+        self.sur = surrogate
+        self.rng = np.random.default_rng(seed)
+        self.eval = Evaluator(ctx, inst, D)
+        dev = D.device
+        self.cur = torch.tensor(np.asarray(start, dtype=np.int32), device=dev)
+        self.cur_cost = float(self.eval(self.cur.view(1, -1))[0].item())
+        self.moves = torch.empty((self.M, 3), dtype=torch.int32, device=dev)
+        self.cand = torch.empty((self.M, self.n), dtype=torch.int32, device=dev)
+        self.top = torch.empty((k, self.n), dtype=torch.int32, device=dev)
+        self.idx = torch.empty(k, dtype=torch.int32, device=dev)
+        self.scores = torch.empty(self.M, dtype=torch.float32, device=dev)
+        self.retrain_every = retrain_every
+        self.scale = scale
+        self.lr = lr
+        self.new_tours, self.new_costs = [], []
+        self.log = SearchLog()
+
+    def step(self):
+        import torch
+        self.moves.copy_(torch.from_numpy(random_moves(self.rng, self.M, self.n)))
+        cvrpsd_neighbors(self.ctx, self.cur, self.moves, self.cand)
+        if self.sur is not None:
+            self.sur.predict(self.cand, self.scores)
+            cvrpsd_topk(self.ctx, self.scores, self.k, self.idx)
+            cvrpsd_gather_tours(self.ctx, self.cand, self.idx, self.top)
+            chosen = self.top
+        else:
+            chosen = self.cand[: self.k]
+        costs = self.eval(chosen)
+        b = int(torch.argmin(costs).item())
+        c = float(costs[b].item())
+        if c < self.cur_cost:
+            self.cur.copy_(chosen[b])
+            self.cur_cost = c
+        self.log.screened += self.M
+        self.log.evaluated += self.k
+        self.log.costs.append(self.cur_cost)
+        if self.sur is not None and self.retrain_every:
+            self.new_tours.append(chosen.clone())
+            self.new_costs.append(costs.to(torch.float32).clone())
+            if len(self.new_tours) >= self.retrain_every:
+                tours = torch.cat(self.new_tours)
+                target = (torch.cat(self.new_costs) - self.scale[0]) / self.scale[1]
+                for _ in range(4):
+                    self.sur.train_step(tours, target, self.lr)
+                self.new_tours, self.new_costs = [], []
+
+    def run(self, iterations: int) -> SearchLog:
+        import torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iterations):
+            self.step()
+        torch.cuda.synchronize()
+        self.log.seconds += time.perf_counter() - t0
+        return self.log
+
+
+def training_set(ctx, inst, D, count: int, seed: int = 0, chain: int = 64, chunk: int = 4096):
+    """`count` (tour, exact SAA cost) pairs: neighbours of a chain of base
+    tours that improves step by step from a random permutation (so the set
+    spans random to locally improved tours). Returns device tensors."""
+    import torch
+    rng = np.random.default_rng(seed)
+    dev = D.device
+    n = inst.n
+    ev = Evaluator(ctx, inst, D)
+    base = torch.tensor(rng.permutation(np.arange(1, n + 1)).astype(np.int32), device=dev)
+    base_cost = float(ev(base.view(1, -1))[0].item())
+    per_base = max(1, count // chain)
+    tours = torch.empty((count, n), dtype=torch.int32, device=dev)
+    costs = torch.empty(count, dtype=torch.float64, device=dev)
+    filled = 0
+    while filled < count:
+        m = min(per_base, count - filled)
+        moves = torch.from_numpy(random_moves(rng, m, n)).to(dev)
+        cvrpsd_neighbors(ctx, base, moves, tours[filled:filled + m])
+        for a in range(filled, filled + m, chunk):
+            b = min(filled + m, a + chunk)
+            costs[a:b] = ev(tours[a:b])
+        block = costs[filled:filled + m]
+        j = int(torch.argmin(block).item())
+        if float(block[j].item()) < base_cost:       # move the base downhill
+            base = tours[filled + j].clone()
+            base_cost = float(block[j].item())
+        filled += m
+    return tours, costs
+
+
+def tour_lengths(tours_host: np.ndarray, dist: np.ndarray) -> np.ndarray:
+    """Closed lengths (depot, tour, depot) of host tours [T][n]."""
+    t = np.asarray(tours_host, dtype=np.int64)
+    d = np.asarray(dist, dtype=np.int64)
+    return d[0, t[:, 0]] + d[t[:, -1], 0] + d[t[:, :-1], t[:, 1:]].sum(axis=1)
+
+
+def train_surrogate(sur: Surrogate, tours, costs, *, dist=None, epochs: int = 8, batch: int = 1024,
+                    lr: float = 1e-3, seed: int = 0, holdout: float = 0.1):
+    """Fit the surrogate to standardised costs (the tour-length input is
+    standardised over the same tours when `dist` is given); returns (mean, sd)
+    of the costs and the held-out mean absolute error in cost units."""
+    import torch
+    N = int(tours.shape[0])
+    if dist is not None:
+        lens = tour_lengths(tours.cpu().numpy(), dist).astype(np.float64)
+        sur.set_scale(float(lens.mean()), float(lens.std() + 1e-9))
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    perm = torch.randperm(N, generator=g).to(tours.device)
+    n_hold = int(N * holdout)
+    hold, train = perm[:n_hold], perm[n_hold:]
+    c32 = costs.to(torch.float32)
+    mean, sd = float(c32[train].mean().item()), float(c32[train].std().item())
+    target = (c32 - mean) / sd
+    steps = 0
+    total = epochs * ((len(train) + batch - 1) // batch)
+    for ep in range(epochs):
+        order = train[torch.randperm(len(train), generator=g).to(tours.device)]
+        for a in range(0, len(order), batch):
+            ix = order[a:a + batch]
+            rate = lr * (0.1 + 0.9 * (1.0 - steps / total))    # linear decay to 10 %
+            sur.train_step(tours[ix].contiguous(), target[ix].contiguous(), rate)
+            steps += 1
+    pred = torch.empty(n_hold, dtype=torch.float32, device=tours.device)
+    sur.predict(tours[hold].contiguous(), pred)
+    mae = float(((pred * sd + mean) - c32[hold]).abs().mean().item())
+    return (mean, sd), mae

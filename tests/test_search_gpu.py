@@ -1,0 +1,188 @@
+"""GPU tests of the local-search pieces: the many-tours Split, neighbour
+moves, top-k, the surrogate network's kernels (against the FP64 reference)
+and what the trained surrogate gains over unscreened neighbour choice."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_reference as M
+from synth import demand_matrix, make_instance, workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18022_gb300 import build
+    build.build()
+    import paper_2511_18022_gb300 as m
+    return m
+
+
+@pytest.fixture()
+def sp(cv):
+    s = cv.Splitter(0)
+    yield s
+    s.close()
+
+
+def apply_move(tour, t, a, b):
+    tour = list(tour)
+    if t == 0:
+        lo, hi = min(a, b), max(a, b)
+        tour[lo:hi + 1] = tour[lo:hi + 1][::-1]
+        return tour
+    c = tour.pop(a)
+    tour.insert(b, c)
+    return tour
+
+
+def test_split_eval_tours_matches_oracle(sp, cv):
+    w = workload("corr-n200", S=3001)
+    inst = w.instances[0]
+    D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 3001, dtype=np.int16)
+    D[11, 7] = inst.Q + 3
+    rng = np.random.default_rng(0)
+    tours = np.stack([inst.tour] + [rng.permutation(np.arange(1, inst.n + 1)) for _ in range(9)]).astype(np.int32)
+    dT = torch.from_numpy(tours).cuda()
+    dD = torch.from_numpy(D).cuda()
+    mean = torch.empty(10, dtype=torch.float64, device="cuda")
+    sums = torch.empty(10, dtype=torch.int64, device="cuda")
+    inf = torch.empty(10, dtype=torch.int64, device="cuda")
+    cv.cvrpsd_split_eval_tours(sp.ctx, dT, inst.dist, dD, inst.Q, inst.L, mean=mean, sums=sums, infeasible=inf)
+    for t in range(10):
+        _, ws, wi, _ = oracle.split_costs(tours[t], inst.dist, D, inst.Q, inst.L)
+        assert (int(sums[t]), int(inf[t])) == (ws, wi)
+        assert float(mean[t]) == ws / (3001 - wi)
+
+
+def test_neighbors_and_gather(sp, cv):
+    rng = np.random.default_rng(2)
+    n = 37
+    base = rng.permutation(np.arange(1, n + 1)).astype(np.int32)
+    from paper_2511_18022_gb300.search import random_moves
+    moves = random_moves(rng, 500, n)
+    moves[:3] = [[0, 5, 5], [1, 0, n - 1], [1, n - 1, 0]]
+    out = torch.empty((500, n), dtype=torch.int32, device="cuda")
+    cv.cvrpsd_neighbors(sp.ctx, torch.from_numpy(base).cuda(), torch.from_numpy(moves).cuda(), out)
+    got = out.cpu().numpy()
+    for m in range(500):
+        assert got[m].tolist() == apply_move(base, *moves[m]), m
+    idx = torch.tensor([499, 0, 17], dtype=torch.int32, device="cuda")
+    g = torch.empty((3, n), dtype=torch.int32, device="cuda")
+    cv.cvrpsd_gather_tours(sp.ctx, out, idx, g)
+    assert (g.cpu().numpy() == got[[499, 0, 17]]).all()
+
+
+@pytest.mark.parametrize("M,k", [(4096, 64), (1000, 1000), (5, 1), (3000, 17)])
+def test_topk(sp, cv, M, k):
+    rng = np.random.default_rng(M)
+    s = rng.normal(size=M).astype(np.float32)
+    s[rng.integers(0, M, M // 10)] = 0.25                # ties
+    if M > 10:
+        s[3] = np.nan
+    out = torch.empty(k, dtype=torch.int32, device="cuda")
+    cv.cvrpsd_topk(sp.ctx, torch.from_numpy(s).cuda(), k, out)
+    key = np.where(np.isnan(s), np.inf, s)
+    want = np.lexsort((np.arange(M), key))[:k]
+    assert out.cpu().numpy().tolist() == want.tolist()
+
+
+def surrogate_case(cv, sp, T=48, n=60, seed=0):
+    inst = make_instance(n, 5, 20, seed=seed, Q=64)
+    rng = np.random.default_rng(seed)
+    cust = np.column_stack([inst.coords[1:, 0], inst.coords[1:, 1], inst.mu,
+                            rng.uniform(1, 6, n)]).astype(np.float32)
+    sur = cv.Surrogate(sp.ctx, cust, inst.dist, Q=64.0, seed=seed + 1)
+    tours = np.stack([rng.permutation(np.arange(1, n + 1)) for _ in range(T)]).astype(np.int32)
+    target = rng.normal(size=T).astype(np.float32)
+    return inst, cust, sur, tours, target
+
+
+def test_surrogate_forward_matches_reference(sp, cv):
+    inst, cust, sur, tours, _ = surrogate_case(cv, sp)
+    p = sur.params()
+    phi, t = M.features(tours, cust, inst.dist, Q=64.0)   # Q = 2^6 keeps the features exact in fp32
+    want, _ = M.forward(p, phi, t, bf16=True)
+    out = torch.empty(len(tours), dtype=torch.float32, device="cuda")
+    sur.predict(torch.from_numpy(tours).cuda(), out)
+    assert np.allclose(out.cpu().numpy(), want, rtol=1e-4, atol=1e-4)
+    sur.close()
+
+
+def test_surrogate_scaled_length_matches_reference(sp, cv):
+    inst, cust, sur, tours, _ = surrogate_case(cv, sp, seed=9)
+    sur.set_scale(30000.0, 1024.0)
+    p = sur.params()
+    phi, t = M.features(tours, cust, inst.dist, Q=64.0, len_mean=30000.0, len_sd=1024.0)
+    want, _ = M.forward(p, phi, t, bf16=True)
+    out = torch.empty(len(tours), dtype=torch.float32, device="cuda")
+    sur.predict(torch.from_numpy(tours).cuda(), out)
+    assert np.allclose(out.cpu().numpy(), want, rtol=1e-4, atol=1e-4)
+    sur.close()
+
+
+def test_surrogate_gradients_match_reference(sp, cv):
+    inst, cust, sur, tours, target = surrogate_case(cv, sp, seed=3)
+    p = sur.params()
+    phi, t = M.features(tours, cust, inst.dist, Q=64.0)
+    wloss, wg, _ = M.loss_and_grad(p, phi, t, target, bf16=True)
+    g, loss = sur.gradients(torch.from_numpy(tours).cuda(), torch.from_numpy(target).cuda())
+    assert abs(loss - wloss) <= 1e-4 * max(1.0, wloss)
+    for lo, hi in ((M.OFF_W1, M.OFF_B1), (M.OFF_B1, M.OFF_W2), (M.OFF_W2, M.OFF_B2), (M.OFF_B2, M.OFF_W3),
+                   (M.OFF_W3, M.OFF_B3), (M.OFF_B3, M.NPARAMS)):
+        scale = np.abs(wg[lo:hi]).max() + 1e-12
+        assert np.abs(g[lo:hi] - wg[lo:hi]).max() <= 1e-3 * scale, (lo, hi)
+    sur.close()
+
+
+def test_training_reduces_loss(sp, cv):
+    inst, cust, sur, tours, _ = surrogate_case(cv, sp, T=512, seed=5)
+    dT = torch.from_numpy(tours).cuda()
+    phi, t = M.features(tours, cust, inst.dist, Q=64.0)
+    lens = t * 500.0 * inst.n
+    sur.set_scale(float(lens.mean()), float(lens.std()))
+    y = torch.tensor(((lens - lens.mean()) / lens.std()).astype(np.float32)).cuda()   # learnable target
+    _, l0 = sur.gradients(dT, y)
+    for _ in range(200):
+        sur.train_step(dT, y, 3e-3)
+    _, l1 = sur.gradients(dT, y)
+    assert l1 < 0.2 * l0
+    sur.close()
+
+
+def test_surrogate_screening_beats_random_choice(sp, cv):
+    """The trained surrogate's top-64 of 4096 neighbours contain clearly
+    cheaper tours (by the exact Split) than 64 unscreened neighbours."""
+    from paper_2511_18022_gb300 import search
+    w = workload("surrogate-n200", S=4096)
+    inst = w.instances[0]
+    D = torch.empty((inst.n, w.S), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    cust = search.customer_features(inst, D[:, :4096].cpu().numpy())
+    tours, costs = search.training_set(sp.ctx, inst, D, 24_000, seed=1)
+    sur = cv.Surrogate(sp.ctx, cust, inst.dist, Q=float(inst.Q), seed=7)
+    scale, mae = search.train_surrogate(sur, tours, costs, dist=inst.dist, epochs=10)
+    assert mae < 0.5 * float(costs.std().item())
+    rng = np.random.default_rng(3)
+    ev = search.Evaluator(sp.ctx, inst, D)
+    base = tours[int(torch.argmin(costs).item())].clone()
+    gains = []
+    for _ in range(8):
+        moves = torch.from_numpy(search.random_moves(rng, 4096, inst.n)).cuda()
+        cand = torch.empty((4096, inst.n), dtype=torch.int32, device="cuda")
+        cv.cvrpsd_neighbors(sp.ctx, base, moves, cand)
+        scores = torch.empty(4096, dtype=torch.float32, device="cuda")
+        sur.predict(cand, scores)
+        idx = torch.empty(64, dtype=torch.int32, device="cuda")
+        cv.cvrpsd_topk(sp.ctx, scores, 64, idx)
+        top = torch.empty((64, inst.n), dtype=torch.int32, device="cuda")
+        cv.cvrpsd_gather_tours(sp.ctx, cand, idx, top)
+        screened = ev(top).clone()
+        unscreened = ev(cand[:64].contiguous()).clone()
+        gains.append(float(unscreened.mean() - screened.mean()))
+    assert np.mean(gains) > 0 and sum(g > 0 for g in gains) >= 6
+    sur.close()

@@ -296,3 +296,21 @@ def test_zero_break_costs_take_the_general_step(sp, cv):
     for shape in [(256, 1, 16), (128, 2, 32)]:
         sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
         check_parity(sp, inst, D)
+
+
+def test_overflow_then_back_pops_stay_bounded(sp, cv):
+    """The deque grows past its ring along a ray (C_i > 0, increasing g),
+    then a customer next to the depot forces back pops: the overflowed
+    scenario must be set aside (and recomputed), not walked on a ring whose
+    slots were overwritten."""
+    coords = [[0, 0]] + [[3 * k, 4 * k] for k in range(1, 31)] + [[1, 0]] + \
+        [[3 * k, 4 * k] for k in range(31, 40)]
+    n = len(coords) - 1
+    inst = instance_from_coords(coords, list(range(1, n + 1)), Q=1000)
+    D = np.ones((n, 300), np.int16)
+    D[:, 150:] = 2
+    for shape in [(256, 1, 16), (128, 2, 16), (64, 1, 32)]:
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+        check_parity(sp, inst, D, Q=1000, L=n)
+        # the ray's deque peaks near 31 entries: it overflows a 16-entry ring only
+        assert (sp.stats()["overflow"] > 0) == (shape[2] == 16)
