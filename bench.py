@@ -484,6 +484,45 @@ def run_surrogate(args):
     return 0
 
 
+def run_oos(args):
+    """oos-n200: optimise with 1, 100, 1,000 and 10,000 training scenarios and
+    evaluate every result on 10^6 held-out scenarios (Section 4.2's study on a
+    synthetic instance)."""
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2511_18022_gb300 as cv
+    from paper_2511_18022_gb300 import build, search
+    from synth import workload
+
+    build.build()
+    w = workload("surrogate-n200", S=10_000)
+    inst = w.instances[0]
+    sp = cv.Splitter(local)
+    D_train = torch.empty((inst.n, 10_000), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D_train)
+    S_test = args.S or 1_000_000
+    D_test = torch.empty((inst.n, S_test), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0] + 77_777, cv.GEN_CORRELATED, inst.mu, inst.region, D_test)
+    t0 = time.perf_counter()
+    rows = search.oos_study(sp.ctx, inst, D_train, D_test, [1, 100, 1000, 10_000], iterations=args.steps, seed=3)
+    el = time.perf_counter() - t0
+    if rank == 0:
+        print(json.dumps({
+            "metric": "out-of-sample SAA cost of the searched tour vs training scenario count",
+            "value": rows[-1][2], "unit": "cost", "n_gpus": world, "steps": args.steps, "warmup": 0,
+            "ms_per_step": el / (4 * args.steps) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": w.name, "n": inst.n, "Q": inst.Q, "L": inst.L, "S_test": S_test,
+                       "search": "best of 64 random 2-opt/relocate neighbours per iteration, exact GPU Split"},
+            "rows": [{"S_train": r[0], "in_sample": r[1], "out_of_sample": r[2]} for r in rows],
+            "gpu_launches": None,
+        }))
+    sp.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,6 +552,8 @@ def main():
         return run_batched(args)
     if args.workload == "surrogate-n200":
         return run_surrogate(args)
+    if args.workload == "oos-n200":
+        return run_oos(args)
     return run_ours(args)
 
 

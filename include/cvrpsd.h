@@ -64,10 +64,14 @@ extern "C" {
 /* Largest tour the library accepts. */
 #define CVRPSD_MAX_N 8191
 
-/* Kernel choice for the Split (see cvrpsd_config). */
+/* Kernel choice for the Split (see cvrpsd_config). AUTO takes SEQPAR for
+ * S <= 64 scenarios on tours of n >= 128 (lowest latency there) and DEQUE
+ * otherwise. */
 #define CVRPSD_KERNEL_AUTO   0
 #define CVRPSD_KERNEL_DEQUE  1   /* one thread per scenario, monotone deque */
 #define CVRPSD_KERNEL_WARP   2   /* one warp per scenario, parallel window min */
+#define CVRPSD_KERNEL_SEQPAR 3   /* few scenarios: min-plus matrix products over blocks of
+                                    positions, parallel along the tour (S <= 4096) */
 
 /* Demand kinds of the scenario generator. */
 #define CVRPSD_GEN_NORMAL      0

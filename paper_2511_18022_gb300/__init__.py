@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MAX_N,
-                   KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, GEN_NORMAL, GEN_CORRELATED)
+                   KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, KERNEL_SEQPAR, GEN_NORMAL, GEN_CORRELATED)
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
@@ -24,7 +24,7 @@ __all__ = [
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
-    "KERNEL_DEQUE", "KERNEL_WARP", "GEN_NORMAL", "GEN_CORRELATED",
+    "KERNEL_DEQUE", "KERNEL_WARP", "KERNEL_SEQPAR", "GEN_NORMAL", "GEN_CORRELATED",
 ]
 
 INT32_MAX = 2**31 - 1

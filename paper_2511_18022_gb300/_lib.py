@@ -22,7 +22,7 @@ ERR_UNSUPPORTED = -7
 I16 = 2
 I32 = 4
 MAX_N = 8191
-KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP = 0, 1, 2
+KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, KERNEL_SEQPAR = 0, 1, 2, 3
 GEN_NORMAL, GEN_CORRELATED = 0, 1
 
 # Every symbol include/cvrpsd.h declares.

@@ -27,6 +27,7 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("gen_demand.cu", [], "gen_demand.o"),
     ("api.cu", [], "api.o"),
     ("search.cu", [], "search.o"),
+    ("seqpar.cu", [], "seqpar.o"),
     ("mlp.cu", [], "mlp.o"),
     ("search_api.cu", [], "search_api.o"),
     ("noalloc.cu", [], "noalloc.o"),

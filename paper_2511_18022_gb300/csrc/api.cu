@@ -180,6 +180,9 @@ int cvrpsd_destroy(cvrpsd_ctx *ctx)
     if (ctx->mt_acc) cudaFree(ctx->mt_acc);
     if (ctx->mt_list) cudaFree(ctx->mt_list);
     if (ctx->mt_dist) cudaFree(ctx->mt_dist);
+    if (ctx->seq_lo) cudaFree(ctx->seq_lo);
+    if (ctx->seq_flags) cudaFree(ctx->seq_flags);
+    if (ctx->seq_mats) cudaFree(ctx->seq_mats);
     delete ctx;
     return CVRPSD_OK;
 }
@@ -187,7 +190,7 @@ int cvrpsd_destroy(cvrpsd_ctx *ctx)
 int cvrpsd_set_config(cvrpsd_ctx *ctx, const cvrpsd_config *cfg)
 {
     if (!ctx || !cfg) return CVRPSD_ERR_ARG;
-    if (cfg->kernel < CVRPSD_KERNEL_AUTO || cfg->kernel > CVRPSD_KERNEL_WARP)
+    if (cfg->kernel < CVRPSD_KERNEL_AUTO || cfg->kernel > CVRPSD_KERNEL_SEQPAR)
         return fail(ctx, CVRPSD_ERR_ARG, "kernel %d unknown", cfg->kernel);
     const bool any_shape = cfg->threads || cfg->spt || cfg->ring;
     if (any_shape && !valid_shape(cfg->threads, cfg->spt, cfg->ring))
@@ -293,9 +296,60 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
     const bool timed = ctx->profiling && (out_sum || out_infeasible || out_mean) && S > 0;
     bool fallback_launched = false;
     if (S > 0) {
-        const int kernel = ctx->cfg.kernel == CVRPSD_KERNEL_AUTO ? CVRPSD_KERNEL_DEQUE : ctx->cfg.kernel;
+        // Automatic choice: for a handful of scenarios on a long tour the
+        // sequence-parallel kernel has the lowest latency (it parallelises
+        // along the tour); otherwise scenario parallelism wins.
+        int kernel = ctx->cfg.kernel;
+        if (kernel == CVRPSD_KERNEL_AUTO)
+            kernel = (S <= 64 && n >= 128 && !pred) ? CVRPSD_KERNEL_SEQPAR : CVRPSD_KERNEL_DEQUE;
         const int warp_grid = 2 * (ctx->sm_count > 0 ? ctx->sm_count : 152);
-        if (kernel == CVRPSD_KERNEL_WARP) {
+        if (kernel == CVRPSD_KERNEL_SEQPAR && !pred) {
+            if (S > 4096) return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "the sequence-parallel kernel takes S <= 4096");
+            const int blocks = seqpar_blocks(n), W = seqpar_width();
+            int rc2 = 0;
+            auto grow = [&](int32_t **buf, long long *cap, long long need, const char *what) {
+                if (rc2 || need <= *cap) return;
+                if (*buf) cudaFree(*buf);
+                *buf = nullptr;
+                *cap = 0;
+                if (cudaMalloc(buf, sizeof(int32_t) * need) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc2 = fail(ctx, CVRPSD_ERR_NOMEM, "%s", what);
+                    return;
+                }
+                *cap = need;
+            };
+            grow(&ctx->seq_lo, &ctx->seq_lo_cap, S * (long long)n, "window starts");
+            grow(&ctx->seq_flags, &ctx->seq_flags_cap, S, "flags");
+            grow(&ctx->seq_mats, &ctx->seq_mats_cap, S * (long long)blocks * W * W, "transfer matrices");
+            if (rc2) return rc2;
+            SeqParParams a{};
+            a.tab = ctx->d_tab;
+            a.demand = demand;
+            a.ld = ld;
+            a.S = (int)S;
+            a.n = n;
+            a.Q = Q;
+            a.L = L;
+            a.g0 = g0;
+            a.blocks = blocks;
+            a.lo = ctx->seq_lo;
+            a.flags = ctx->seq_flags;
+            a.mats = ctx->seq_mats;
+            a.out_cost = out_cost;
+            a.acc = ctx->d_acc;
+            a.list = ctx->d_list;
+            if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
+            CK(launch_seqpar(a, demand_dtype, stream), "seqpar launch");
+            if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
+            CK(launch_split_warp(p, demand_dtype, ctx->d_list, ctx->d_acc + ACC_OVERFLOW, warp_grid, ctx->max_smem,
+                                 stream),
+               "split_warp (set-aside scenarios) launch");
+            if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
+            fallback_launched = true;
+            st.kernel = CVRPSD_KERNEL_SEQPAR;
+            st.launches = 4;
+        } else if (kernel == CVRPSD_KERNEL_WARP) {
             long long need = (S + 3) / 4;
             const int grid = (int)(need < 8LL * warp_grid ? need : 8LL * warp_grid);
             if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");

@@ -42,6 +42,13 @@ struct cvrpsd_ctx {
     long long mt_list_cap = 0;
     int32_t *mt_dist = nullptr;
     long long mt_dist_cap = 0;
+    // sequence-parallel Split scratch
+    int32_t *seq_lo = nullptr;
+    long long seq_lo_cap = 0;
+    int32_t *seq_flags = nullptr;
+    long long seq_flags_cap = 0;
+    int32_t *seq_mats = nullptr;
+    long long seq_mats_cap = 0;
 };
 
 namespace cvrpsd {

@@ -111,6 +111,24 @@ cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeS
 cudaError_t launch_split_warp_batch(const BatchParams &b, int esize, int grid_ctas, int max_smem, bool configure_only,
                                     cudaStream_t stream);
 
+// Sequence-parallel Split for few scenarios (seqpar.cu).
+struct SeqParParams {
+    const TourStep *tab;          // device [n]
+    const void *demand;           // device [n][ld]
+    long long ld;
+    int S, n, Q, L, g0;
+    int blocks;                   // ceil(n / block)
+    int32_t *lo;                  // scratch [S][n]: window starts
+    int32_t *flags;               // scratch [S]: nonzero = hand to the warp kernel
+    int32_t *mats;                // scratch [S][blocks][W][W]: block transfer matrices
+    int32_t *out_cost;            // device [S] or nullptr
+    unsigned long long *acc;      // device [ACC_WORDS]
+    int32_t *list;                // device [S]: scenarios for the warp kernel
+};
+cudaError_t launch_seqpar(const SeqParParams &a, int esize, cudaStream_t st);
+int seqpar_blocks(int n);
+int seqpar_width();
+
 // Local search on the device (search.cu).
 cudaError_t launch_neighbors(const int32_t *base, int n, const int32_t *moves, int M, int32_t *out, cudaStream_t st);
 cudaError_t launch_tour_tables(const int32_t *tours, int T, int n, const int32_t *dist, int32_t *D_out,

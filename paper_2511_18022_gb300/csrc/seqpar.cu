@@ -1,0 +1,157 @@
+// Sequence-parallel Split for few scenarios: the recursion over tour
+// positions as a product of min-plus matrices (the abstract's "min-plus
+// matrix-vector products over layered DAGs", parallel along the positions
+// rather than across scenarios).
+//
+// With g(p) = f(p) + c(0, sigma_{p+1}) - D[p+1] the recursion is
+// g(i) = C_i + min_{p in W(i)} g(p). The state after position i is the vector
+// x_i = (g(i), g(i-1), ..., g(i-W+1)) of the last W values, and
+// x_i = A_i (x) x_{i-1} in the (min, +) semiring: row 0 of A_i holds C_i at the
+// columns of the window W(i) = [lo(i), i-1] and +inf elsewhere, the other rows
+// shift the state down. The positions are cut into blocks of kSeqBlock; the
+// transfer matrix of each block (a kSeqW x kSeqW min-plus matrix) is built
+// independently, in parallel over blocks and over its columns; a last pass
+// folds the block matrices over the initial state x_0 = (g(0), +inf, ...).
+// f(n) comes out as row 0 of the final state, position n using C_n = D[n] +
+// c(sigma_n, 0). A scenario whose window is longer than kSeqW, or with a
+// demand above Q or below 0, is handed to the warp kernel.
+#include <stdint.h>
+
+#include "kernels.h"
+#include "tour_table.h"
+
+namespace cvrpsd {
+
+constexpr int kSeqW = 64;        // state width (longest window handled)
+constexpr int kSeqBlock = 64;    // positions per block
+constexpr int kInf = 0x3FFFFFFF;
+
+__device__ __forceinline__ int sat_add(int a, int b) { return (a >= kInf || b >= kInf) ? kInf : a + b; }
+
+// Window starts: lo[s][i-1] = smallest p >= i - L with P(i) - P(p) <= Q.
+// One block per scenario; flags[s] = 1 if the scenario must go elsewhere.
+template <typename DT>
+__global__ void seqpar_windows_kernel(SeqParParams a)
+{
+    extern __shared__ int P[];                    // [n + 1] prefix loads
+    const int n = a.n, s = blockIdx.x;
+    if (s >= a.S) return;
+    const DT *dem = reinterpret_cast<const DT *>(a.demand);
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = 1 + threadIdx.x; i <= n; i += blockDim.x) {
+        int q = (int)dem[(long long)(a.tab[i - 1].row & kRowMask) * a.ld + s];
+        if (q < 0 || q > a.Q) { atomicOr(&s_bad, 1); q = 0; }
+        P[i] = q;
+    }
+    if (threadIdx.x == 0) P[0] = 0;
+    __syncthreads();
+    // inclusive scan (one warp walks the chunks; n is at most a few thousand)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int carry = 0;
+        for (int b = 1; b <= n; b += 32) {
+            const int i = b + lane;
+            int v = i <= n ? P[i] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (i <= n) P[i] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    int too_long = 0;
+    for (int i = 1 + threadIdx.x; i <= n; i += blockDim.x) {
+        int lo = i - a.L > 0 ? i - a.L : 0, hi = i - 1;   // P(i) - P(i-1) <= Q always (bad demands zeroed)
+        while (lo < hi) {                                 // first p in [lo, hi] with P(i) - P(p) <= Q
+            const int mid = (lo + hi) >> 1;
+            if (P[i] - P[mid] <= a.Q) hi = mid; else lo = mid + 1;
+        }
+        a.lo[(long long)s * n + (i - 1)] = lo;
+        too_long |= (i - lo) > kSeqW;
+    }
+    if (too_long) atomicOr(&s_bad, 2);
+    __syncthreads();
+    if (threadIdx.x == 0) a.flags[s] = s_bad;
+}
+
+// Transfer matrix of block b of scenario s: kSeqW threads, thread j owns
+// column j (the image of unit state j); rows live in a circular buffer.
+__global__ void __launch_bounds__(kSeqW) seqpar_block_kernel(SeqParParams a)
+{
+    __shared__ int Mx[kSeqW][kSeqW + 1];          // [row slot][column]
+    const int s = blockIdx.y, b = blockIdx.x, j = threadIdx.x, n = a.n;
+    if (s >= a.S || a.flags[s]) return;
+    const int i0 = b * kSeqBlock + 1, i1 = min(n, i0 + kSeqBlock - 1);
+    for (int r = 0; r < kSeqW; ++r) Mx[r][j] = r == j ? 0 : kInf;    // identity
+    int head = 0;                                  // slot of state row 0
+    for (int i = i0; i <= i1; ++i) {
+        const int len = i - a.lo[(long long)s * n + (i - 1)];      // window rows 0..len-1
+        int m = kInf;
+        for (int r = 0; r < len; ++r) m = min(m, Mx[(head + r) & (kSeqW - 1)][j]);
+        const int row0 = sat_add(m, a.tab[i - 1].c);
+        head = (head - 1) & (kSeqW - 1);           // shift: old rows move down by one
+        Mx[head][j] = row0;
+    }
+    int *out = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
+    for (int r = 0; r < kSeqW; ++r) out[r * kSeqW + j] = Mx[(head + r) & (kSeqW - 1)][j];
+}
+
+// Fold the block matrices over x_0 and write f(n); one warp pair per scenario.
+__global__ void __launch_bounds__(kSeqW) seqpar_fold_kernel(SeqParParams a)
+{
+    __shared__ int x[kSeqW];
+    __shared__ long long s_sum;
+    const int s = blockIdx.x, r = threadIdx.x;
+    if (s >= a.S) return;
+    if (a.flags[s]) {                              // handed to the warp kernel
+        if (r == 0) {
+            const unsigned long long idx = atomicAdd(a.acc + ACC_OVERFLOW, 1ull);
+            a.list[idx] = s;
+        }
+        return;
+    }
+    x[r] = r == 0 ? a.g0 : kInf;
+    __syncthreads();
+    for (int b = 0; b < a.blocks; ++b) {
+        const int *M = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
+        int v = kInf;
+        for (int c = 0; c < kSeqW; ++c) v = min(v, sat_add(M[r * kSeqW + c], x[c]));
+        __syncthreads();
+        x[r] = v;
+        __syncthreads();
+    }
+    if (r == 0) {
+        const int cost = x[0];
+        if (a.out_cost) a.out_cost[s] = cost;
+        atomicAdd(a.acc + ACC_SUM, (unsigned long long)cost);
+    }
+}
+
+cudaError_t launch_seqpar(const SeqParParams &a, int esize, cudaStream_t st)
+{
+    const size_t smem = (size_t)(a.n + 1) * sizeof(int);
+    if (esize == 2) {
+        cudaError_t e = cudaFuncSetAttribute(seqpar_windows_kernel<int16_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        seqpar_windows_kernel<int16_t><<<(unsigned)a.S, 256, smem, st>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(seqpar_windows_kernel<int32_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        seqpar_windows_kernel<int32_t><<<(unsigned)a.S, 256, smem, st>>>(a);
+    }
+    seqpar_block_kernel<<<dim3((unsigned)a.blocks, (unsigned)a.S), kSeqW, 0, st>>>(a);
+    seqpar_fold_kernel<<<(unsigned)a.S, kSeqW, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int seqpar_blocks(int n) { return (n + kSeqBlock - 1) / kSeqBlock; }
+int seqpar_width() { return kSeqW; }
+
+}  // namespace cvrpsd

@@ -206,3 +206,22 @@ def train_surrogate(sur: Surrogate, tours, costs, *, dist=None, epochs: int = 8,
     sur.predict(tours[hold].contiguous(), pred)
     mae = float(((pred * sd + mean) - c32[hold]).abs().mean().item())
     return (mean, sd), mae
+
+
+def oos_study(ctx, inst, D_train, D_test, S_list, *, iterations: int = 400, seed: int = 0, k: int = 64):
+    """Out-of-sample effect of the scenario count (the study of Section 4.2
+    on a synthetic instance): for each S in S_list, local search with the
+    exact Split on the first S training scenarios, from one common start;
+    the final tour is then split under the held-out scenarios D_test.
+    Returns rows (S, in-sample SAA cost, out-of-sample SAA cost)."""
+    import torch
+    start = np.random.default_rng(seed).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    test_eval = Evaluator(ctx, inst, D_test)
+    rows = []
+    for S in S_list:
+        Dtr = D_train[:, :S].contiguous()
+        ls = LocalSearch(ctx, inst, Dtr, start, k=k, seed=seed + 1)
+        ls.run(iterations)
+        oos = float(test_eval(ls.cur.view(1, -1))[0].item())
+        rows.append((int(S), ls.cur_cost, oos))
+    return rows

@@ -186,3 +186,19 @@ def test_surrogate_screening_beats_random_choice(sp, cv):
         gains.append(float(unscreened.mean() - screened.mean()))
     assert np.mean(gains) > 0 and sum(g > 0 for g in gains) >= 6
     sur.close()
+
+
+def test_more_training_scenarios_generalise_better(sp, cv):
+    """Section 4.2's observation on a synthetic instance: a tour optimised on
+    one scenario does worse on held-out scenarios than one optimised on a
+    thousand."""
+    from paper_2511_18022_gb300 import search
+    w = workload("surrogate-n200", S=1000)
+    inst = w.instances[0]
+    D_train = torch.empty((inst.n, 1000), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D_train)
+    D_test = torch.empty((inst.n, 100_000), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0] + 5, cv.GEN_CORRELATED, inst.mu, inst.region, D_test)
+    rows = search.oos_study(sp.ctx, inst, D_train, D_test, [1, 1000], iterations=150, seed=2)
+    (s1, in1, out1), (s2, in2, out2) = rows
+    assert out2 < out1
