@@ -50,10 +50,11 @@ cudaError_t launch_split_deque_i16_nocap(const SplitParams &p, const DequeShape 
 cudaError_t launch_split_deque_i32_cap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
 cudaError_t launch_split_deque_i32_nocap(const SplitParams &p, const DequeShape &s, cudaStream_t st);
 
-// Rings ([spt][ring][threads] int2) followed by the tour table.
+// Dynamic shared memory of the deque kernel: its rings ([spt][ring][threads] int2).
 inline size_t split_deque_smem(const SplitParams &p, const DequeShape &shape)
 {
-    return (size_t)shape.spt * shape.ring * shape.threads * 8 + (size_t)p.n * sizeof(TourStep);
+    (void)p;
+    return (size_t)shape.spt * shape.ring * shape.threads * 8;
 }
 
 // Warp-per-scenario kernel. If `list` is non-null it evaluates the scenarios

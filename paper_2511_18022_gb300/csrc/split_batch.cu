@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
         int2 *list = b.list;
         const long long cap = b.list_cap;
         long long sum = split_thread<DT, SPT, R, T, LCAP>(
-            td.demand, td.ld, b.S, s_first, td.n, td.Q, td.L, td.K, td.g0, sbase, tab, tid, td.out_cost,
+            td.demand, td.ld, b.S, s_first, td.n, td.Q, td.L, td.K, td.g0, sbase, TabShared{tab}, tid, td.out_cost,
             [acc, list, cap, t](long long s) {
                 const unsigned long long idx = atomicAdd(acc + BACC_LIST, 1ull);
                 if ((long long)idx < cap) list[idx] = make_int2(t, (int)s);

@@ -95,6 +95,21 @@ __device__ __forceinline__ void sts2(uint32_t a, int x, int y)
     asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y) : "memory");
 }
 
+// Tour table (TourStep = {row, c}, entry i-1 for position i) as the walk
+// reads it: from a shared-memory copy, or straight from global memory with
+// read-only loads. Every lane of a block reads the same entry (all threads
+// walk the same tour position), so either way a read is one broadcast.
+struct TabShared {
+    uint32_t a;   // shared-window address of entry 0
+    __device__ __forceinline__ int row(int i) const { return lds1(a + (uint32_t)(i - 1) * 8u); }
+    __device__ __forceinline__ int c(int i) const { return lds1(a + (uint32_t)(i - 1) * 8u + 4u); }
+};
+struct TabGlobal {
+    const int *p;   // entry 0 as two ints (row, c)
+    __device__ __forceinline__ int row(int i) const { return __ldg(p + 2 * (i - 1)); }
+    __device__ __forceinline__ int c(int i) const { return __ldg(p + 2 * (i - 1) + 1); }
+};
+
 template <int R, int T>
 struct Ring {
     static constexpr uint32_t kStride = T * 8u;            // bytes between slots of one thread
@@ -158,6 +173,8 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
             pb = pb & (PRED ? below > gi : below >= gi);
         }
         d.boff = RG::next(d.boff);
+        // the new back slot is the front's: the ring already holds R entries
+        d.ovf |= d.boff == d.hoff;
     } else {
         // back pops may reach the front: the new entry then becomes the front
         bool empty = false;
@@ -171,14 +188,16 @@ __device__ __forceinline__ int dq_step(Deque &d, uint32_t ring, int q, int i, in
             pb = pb & !emp & (PRED ? below > gi : below >= gi);
         }
         d.boff = RG::next(d.boff);
+        d.ovf |= (d.boff == d.hoff) & !empty;
         d.hoff = empty ? d.boff : d.hoff;
         d.fg = empty ? gi : d.fg;
         d.fx = empty ? x : d.fx;
         if (LCAP) d.fe = empty ? i + L + 1 : d.fe;
     }
+    // On overflow this store overwrites the front slot; the front itself
+    // is held in registers and the scenario is frozen and set aside.
     sts2(ring + d.boff, gi, (int)x);
     d.bg = gi;
-    d.ovf |= RG::next(d.boff) == d.hoff;        // ring full: the next push would overwrite the front
     return gi;
 }
 
@@ -218,20 +237,18 @@ __device__ __forceinline__ void block_accumulate(long long sum, unsigned inf, un
 }
 
 // Positions of one prefetch block. GUARD: the block may run past n; the last
-// position reads f(n) instead of pushing. `tab` is the shared address of the
-// tour table (TourStep = {row, c}); the block's first row carries the
-// host's flag for a C_i <= 0 inside the block.
-template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool GENERAL, bool PRED>
+// position reads f(n) instead of pushing. `tab` reads the tour table; the
+// block's first row carries the host's flag for a C_i <= 0 inside the block.
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool GENERAL, bool PRED, typename TB>
 __device__ __forceinline__ void walk_steps(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
-                                           uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
+                                           const TB &tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
                                            int (&out)[SPT], int16_t *pred, long long ldp)
 {
-    const uint32_t t0 = tab + (uint32_t)(i0 - 1) * 8u + 4u;
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = i0 + u;
         if (GUARD && i > n) break;
-        const int ci = lds1(t0 + 8u * u);
+        const int ci = tab.c(i);
         const uint32_t xi = QK + (uint32_t)i;
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
@@ -243,12 +260,12 @@ __device__ __forceinline__ void walk_steps(Deque (&d)[SPT], const uint32_t (&rin
     }
 }
 
-template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool PRED>
+template <typename DT, int SPT, int R, int T, bool LCAP, bool GUARD, bool PRED, typename TB>
 __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&ring)[SPT], const int (&q)[kPrefetch][SPT],
-                                           uint32_t tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
+                                           const TB &tab, int i0, int n, uint32_t K, uint32_t QK, int L, int Q,
                                            int (&out)[SPT], int16_t *pred, long long ldp)
 {
-    if (lds1(tab + (uint32_t)(i0 - 1) * 8u) & kRowFlagNonPositive)
+    if (tab.row(i0) & kRowFlagNonPositive)
         walk_steps<DT, SPT, R, T, LCAP, GUARD, true, PRED>(d, ring, q, tab, i0, n, K, QK, L, Q, out, pred, ldp);
     else
         walk_steps<DT, SPT, R, T, LCAP, GUARD, false, PRED>(d, ring, q, tab, i0, n, K, QK, L, Q, out, pred, ldp);
@@ -256,27 +273,27 @@ __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&rin
 
 // Demands of positions i0 .. i0 + kPrefetch - 1. Positions past n re-read row
 // n (in bounds, unused), which keeps the loads free of branches.
-template <typename DT, int SPT, bool CLAMP = true>
-__device__ __forceinline__ void prefetch_block(const char *base, uint32_t tab, int i0, int n, uint32_t ldb,
+template <typename DT, int SPT, bool CLAMP = true, typename TB>
+__device__ __forceinline__ void prefetch_block(const char *base, const TB &tab, int i0, int n, uint32_t ldb,
                                                bool full, int nvalid, int (&q)[kPrefetch][SPT])
 {
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = CLAMP ? min(i0 + u, n) : i0 + u;
-        load_demands<DT, SPT>(base, lds1(tab + (uint32_t)(i - 1) * 8u) & kRowMask, ldb, full, nvalid, q[u]);
+        load_demands<DT, SPT>(base, tab.row(i) & kRowMask, ldb, full, nvalid, q[u]);
     }
 }
 
 // The walk of one thread: SPT adjacent scenarios s_first.. of one tour whose
-// table (TourStep = {row, c}) is at shared address `tab`; the rings start at
+// table `tab` is read through TabShared or TabGlobal; the rings start at
 // shared address `rings`. Writes f(n) of feasible scenarios to out_cost (if
 // given), returns the sum of those costs, and passes every scenario it sets
 // aside to `set_aside(s)`. Threads with no scenario (s_first >= S) walk
 // column 0 and report nothing: every lane must take part in the pop votes.
-template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside, bool PRED = false>
+template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside, bool PRED = false, typename TB>
 __device__ __forceinline__ long long split_thread(const void *demand, long long ld, long long S, long long s_first,
                                                   int n, int Q, int L, uint32_t K, int g0, uint32_t rings,
-                                                  uint32_t tab, int tid, int32_t *out_cost, SetAside set_aside,
+                                                  TB tab, int tid, int32_t *out_cost, SetAside set_aside,
                                                   int16_t *pred_base = nullptr, long long ldp = 0)
 {
     using RG = Ring<R, T>;
@@ -348,15 +365,14 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
 template <typename DT, int SPT, int R, int T, bool LCAP, bool PRED = false>
 __global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];   // SPT rings of R*T*8 bytes
     const int n = p.n;
-    // rings first (SPT regions of R*T*8 bytes), then the tour table
-    TourStep *tabp = reinterpret_cast<TourStep *>(smem + (size_t)SPT * R * T * 8);
     const int tid = threadIdx.x;
-    for (int k = tid; k < n; k += T) tabp[k] = p.tab[k];
-    __syncthreads();
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    const uint32_t tab = sbase + (uint32_t)SPT * R * T * 8;
+    // The tour table stays in global memory (L1-resident, one broadcast per
+    // read): shared memory holds only the rings, which leaves room for more
+    // resident blocks.
+    const TabGlobal tab{reinterpret_cast<const int *>(p.tab)};
     const long long s_first = ((long long)blockIdx.x * T + tid) * SPT;
     unsigned long long *acc = p.acc;
     int32_t *list = p.ovf_list;
