@@ -151,6 +151,32 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n,
                       int64_t *out_infeasible, double *out_mean, void *stream);
 
 /*
+ * cvrpsd_split_eval on HOST buffers: the scenario matrix stays in host
+ * memory (an addition of this library, not a step of the paper's method).
+ *
+ *  demand    HOST [n][ld], page-locked and mapped into the device's address
+ *            space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with
+ *            cudaHostRegisterMapped). The kernels read it in place across
+ *            the host link: every demand crosses the link exactly once, with
+ *            no staging copy in device memory.
+ *  out_cost  HOST int32[S] or NULL, page-locked and mapped like `demand`;
+ *            written in place by the kernels.
+ *  other arguments as for cvrpsd_split_eval.
+ *
+ * Always waits for `stream` before returning (the kernels use the host
+ * buffers until then), so the caller may reuse or free them afterwards.
+ * Pageable or unknown memory is rejected with CVRPSD_ERR_ARG; so is a buffer
+ * smaller than [n][ld] / [S] wherever the driver reports the allocation's
+ * extent (the caller guarantees the extent otherwise).
+ */
+int cvrpsd_split_eval_host(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n,
+                           const int32_t *dist, const void *demand,
+                           int32_t demand_dtype, int64_t S, int64_t ld,
+                           int32_t Q, int32_t L, int32_t *out_cost,
+                           int64_t *out_sum, int64_t *out_infeasible,
+                           double *out_mean, void *stream);
+
+/*
  * cvrpsd_split_eval that also recovers the optimal routes (the Section 2
  * Example lists a scenario's routes). For every scenario s and position
  * i = 1..n, pred[(i-1) * ldp + s] (DEVICE int16, [n][ldp], ldp >= S) receives

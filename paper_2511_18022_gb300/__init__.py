@@ -19,7 +19,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_noalloc",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
@@ -139,6 +139,41 @@ def cvrpsd_split_eval(ctx, tour, dist, demand, Q: int, L: int | None = None, *,
     _lib.check(ctx, rc)
     if not host_outputs:
         return SplitResult(rc, None, None, None)
+    return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)
+
+
+def cvrpsd_split_eval_host(ctx, tour, dist, demand, Q: int, L: int | None = None, *, S: int | None = None,
+                           out_cost=None, stream=None) -> SplitResult:
+    """Split one tour under the scenario columns of a page-locked HOST tensor
+    `demand` [n][ld] (torch pin_memory=True). The kernels read it in place
+    across the host link; `out_cost` (optional) is a page-locked host int32
+    tensor of S entries. Waits for the stream; returns the exact sum, the
+    infeasible count and the mean."""
+    import torch
+    tour = _i32(tour)
+    dist = _i32(dist)
+    n = int(tour.shape[0])
+    for t, what in ((demand, "demand"), (out_cost, "out_cost")):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous() or not t.is_pinned():
+            raise CvrpsdError(_lib.ERR_ARG, f"{what} must be a contiguous page-locked host tensor")
+    if demand.dim() != 2 or demand.shape[0] != n:
+        raise CvrpsdError(_lib.ERR_ARG, f"demand must be [n][ld] with n={n}, got {tuple(demand.shape)}")
+    dtype = {torch.int16: I16, torch.int32: I32}.get(demand.dtype)
+    if dtype is None:
+        raise CvrpsdError(_lib.ERR_DTYPE, f"demand must be int16 or int32, got {demand.dtype}")
+    ld = int(demand.shape[1])
+    S = ld if S is None else int(S)
+    if out_cost is not None and (out_cost.dtype != torch.int32 or out_cost.numel() < S):
+        raise CvrpsdError(_lib.ERR_ARG, f"out_cost must be int32 with at least {S} entries")
+    L = n if L is None else int(L)
+    s_sum, s_inf, s_mean = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    rc = _lib.load().cvrpsd_split_eval_host(ctx, tour.ctypes.data, n, dist.ctypes.data, demand.data_ptr(), dtype,
+                                            S, ld, int(Q), L, None if out_cost is None else out_cost.data_ptr(),
+                                            ctypes.byref(s_sum), ctypes.byref(s_inf), ctypes.byref(s_mean),
+                                            _stream_ptr(stream))
+    _lib.check(ctx, rc)
     return SplitResult(rc, s_sum.value, s_inf.value, s_mean.value)
 
 
@@ -491,6 +526,9 @@ class Splitter:
 
     def split(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
         return cvrpsd_split_eval(self.ctx, tour, dist, demand, Q, L, **kw)
+
+    def split_host(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
+        return cvrpsd_split_eval_host(self.ctx, tour, dist, demand, Q, L, **kw)
 
     def gen_demand(self, seed, kind, mu, region, out, **kw):
         cvrpsd_gen_demand(self.ctx, seed, kind, mu, region, out, **kw)

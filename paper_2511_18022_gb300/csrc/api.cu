@@ -73,6 +73,36 @@ int check_device_buffer(cvrpsd_ctx *ctx, const void *ptr, unsigned long long byt
     return CVRPSD_OK;
 }
 
+// The buffer [ptr, ptr + bytes) must be page-locked host memory mapped into
+// the device's address space (cudaHostAlloc, cudaMallocHost, or
+// cudaHostRegister with cudaHostRegisterMapped); *dev gets the address the
+// kernels use. The extent is checked wherever the driver reports the
+// allocation's range.
+int check_host_buffer(cvrpsd_ctx *ctx, const void *ptr, unsigned long long bytes, const char *what, void **dev)
+{
+    if (!ptr) return fail(ctx, CVRPSD_ERR_ARG, "%s is NULL", what);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, CVRPSD_ERR_ARG, "%s is not known to CUDA", what);
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+        return fail(ctx, CVRPSD_ERR_ARG, "%s must be page-locked, mapped host memory (cudaHostAlloc or "
+                                         "cudaHostRegister)", what);
+    if (GetRangeFn fn = get_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)a.devicePointer) == CUDA_SUCCESS) {
+            const unsigned long long end = (unsigned long long)(uintptr_t)a.devicePointer + bytes;
+            if (end > (unsigned long long)base + size)
+                return fail(ctx, CVRPSD_ERR_ARG, "%s: %llu bytes needed, allocation ends after %llu", what, bytes,
+                            (unsigned long long)(base + size - (CUdeviceptr)a.devicePointer));
+        }
+    }
+    *dev = a.devicePointer;
+    return CVRPSD_OK;
+}
+
 int ensure_scratch(cvrpsd_ctx *ctx, long long S)
 {
     if (!ctx->d_acc) {
@@ -232,7 +262,7 @@ namespace {
 int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
                     int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
                     int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream_ptr, int16_t *pred,
-                    int64_t ldp)
+                    int64_t ldp, bool host_buffers = false)
 {
     if (!ctx) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
@@ -248,7 +278,19 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
     if (L < 1) return fail(ctx, CVRPSD_ERR_ARG, "L = %d must be >= 1", L);
     if (L > n) L = n;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if (S > 0) {
+    if (S > 0 && host_buffers) {
+        // the kernels read the demands (and write the costs) in place, across
+        // the host link: each value crosses it once
+        void *dd = nullptr, *od = nullptr;
+        int rc = check_host_buffer(ctx, demand, ((unsigned long long)(n - 1) * ld + S) * demand_dtype, "demand", &dd);
+        if (rc) return rc;
+        demand = dd;
+        if (out_cost) {
+            rc = check_host_buffer(ctx, out_cost, (unsigned long long)S * 4, "out_cost", &od);
+            if (rc) return rc;
+            out_cost = static_cast<int32_t *>(od);
+        }
+    } else if (S > 0) {
         int rc = check_device_buffer(ctx, demand, ((unsigned long long)(n - 1) * ld + S) * demand_dtype, "demand");
         if (rc) return rc;
         if (out_cost) {
@@ -293,7 +335,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
     cvrpsd_stats st{};
     st.overflow = -1;
     st.kernel_ms = st.fallback_ms = -1.0f;
-    const bool timed = ctx->profiling && (out_sum || out_infeasible || out_mean) && S > 0;
+    const bool timed = ctx->profiling && (out_sum || out_infeasible || out_mean || host_buffers) && S > 0;
     bool fallback_launched = false;
     if (S > 0) {
         // Automatic choice: for a handful of scenarios on a long tour the
@@ -394,7 +436,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
         }
     }
     ctx->stats = st;
-    if (!out_sum && !out_infeasible && !out_mean) return CVRPSD_OK;
+    if (!out_sum && !out_infeasible && !out_mean && !host_buffers) return CVRPSD_OK;
 
     CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, ACC_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        stream),
@@ -431,6 +473,16 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
 {
     return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
                            out_mean, stream, nullptr, 0);
+}
+
+int cvrpsd_split_eval_host(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist,
+                           const void *demand, int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L,
+                           int32_t *out_cost, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
+                           void *stream)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
+                           out_mean, stream, nullptr, 0, true);
 }
 
 int cvrpsd_split_routes(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32_t *dist, const void *demand,
