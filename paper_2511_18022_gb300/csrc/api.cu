@@ -401,10 +401,10 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             st.kernel = CVRPSD_KERNEL_WARP;
             st.launches = 1;
         } else {
-            DequeShape shape{256, 1, 16};
+            DequeShape shape{128, 1, 16};
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
             if (pred && (shape.spt != 1 || shape.threads == 64 || shape.ring == 64))
-                shape = DequeShape{256, 1, 16};      // route recovery shapes
+                shape = DequeShape{128, 1, 16};      // route recovery shapes
             // Vector loads of spt demands need spt-aligned rows and base.
             while (shape.spt > 1 && (ld % shape.spt != 0 ||
                                      (uintptr_t)demand % ((uintptr_t)shape.spt * demand_dtype) != 0))

@@ -93,12 +93,13 @@ struct BatchParams {
     unsigned long long *acc;      // device [BACC_WORDS + 3 T]
     int2 *list;                   // device [list_cap]: set-aside (tour, scenario)
     long long list_cap;
-    int max_n;                    // largest tour (shared-memory table size)
+    int max_n;                    // largest tour
 };
 
 inline size_t split_batch_smem(int max_n, const DequeShape &shape)
 {
-    return (size_t)shape.spt * shape.ring * shape.threads * 8 + (size_t)max_n * sizeof(TourStep);
+    (void)max_n;   // the tour tables are read from global memory
+    return (size_t)shape.spt * shape.ring * shape.threads * 8;
 }
 // Persistent deque kernel over all work items; with configure_only it only
 // sets the kernel's shared-memory limit (call before stream capture) and
