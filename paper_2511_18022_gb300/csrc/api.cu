@@ -409,12 +409,13 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             while (shape.spt > 1 && (ld % shape.spt != 0 ||
                                      (uintptr_t)demand % ((uintptr_t)shape.spt * demand_dtype) != 0))
                 shape.spt >>= 1;
-            // Fit the block's shared memory (tour table + rings) in the device limit.
+            // Fit the block's rings in the device's shared-memory limit.
             while (split_deque_smem(p, shape) > (size_t)ctx->max_smem) {
                 if (shape.spt > 1) shape.spt >>= 1;
                 else if (shape.threads > 64) shape.threads >>= 1;
                 else if (shape.ring > 16) shape.ring >>= 1;
-                else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "tour of %d customers does not fit shared memory", n);
+                else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "no deque shape fits %d bytes of shared memory",
+                                 ctx->max_smem);
             }
             if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
             CK(launch_split_deque(p, demand_dtype, shape, stream), "split_deque launch");
@@ -777,7 +778,7 @@ int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tour
         if (shape.spt > 1) shape.spt = 1;
         else if (shape.ring > 16) shape.ring = 16;
         else if (shape.threads > 128) shape.threads = 128;
-        else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "tour of %d customers does not fit shared memory", max_n);
+        else return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "no batch shape fits %d bytes of shared memory", ctx->max_smem);
     }
     const long long per_tile = (long long)shape.threads * shape.spt;
     const long long tiles = (S + per_tile - 1) / per_tile;

@@ -168,7 +168,7 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
         p.out_cost = out_cost;
         p.acc = acc;
         p.ovf_list = list;
-        DequeShape shape{256, 1, 16};
+        DequeShape shape{128, 1, 16};
         while (split_deque_smem(p, shape) > (size_t)ds.max_smem) {
             if (shape.threads > 64) shape.threads >>= 1;
             else return CVRPSD_ERR_UNSUPPORTED;
