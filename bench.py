@@ -378,9 +378,12 @@ def run_batched(args):
         sp.gen_demand(sd + 7919 * rank, cv.GEN_CORRELATED, inst.mu, inst.region, D)
         mats.append(D)
         tours.append(dict(tour=inst.tour, dist=inst.dist, demand=D, Q=inst.Q, L=inst.L))
+    tuned = None
     if args.shape:
         t_, s_, r_ = (int(x) for x in args.shape.split(","))
         sp.configure(kernel=cv.KERNEL_DEQUE, threads=t_, spt=s_, ring=r_)
+    elif not args.no_tune:
+        tuned = sp.batch_autotune(tours, S)
     b = sp.batch(tours, S)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -419,6 +422,7 @@ def run_batched(args):
                        "demand": "correlated lognormal, int16, one [n_t][S] matrix per tour",
                        "l2": f"inputs larger than L2 ({cells * 2 / 1e9:.1f} GB per step), no flush",
                        "kernel": f"persistent deque threads={st['threads']} spt={st['spt']} ring={st['ring']}",
+                       "shape_source": "fixed" if args.shape else ("autotuned" if tuned else "library default"),
                        "graph": "clear + persistent kernel + set-aside pass + result copy"},
             "roofline": {"bound": "hbm", "achieved": round(algo_bytes / (step_ms / 1e3) / 1e9, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(algo_bytes / (step_ms / 1e3) / 1e9 / peak, 4),

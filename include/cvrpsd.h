@@ -282,6 +282,19 @@ int cvrpsd_batch_results(cvrpsd_batch *batch, int64_t *out_sum, int64_t *out_inf
 
 int cvrpsd_batch_destroy(cvrpsd_batch *batch);
 
+/*
+ * Autotuner of the batched path: for every launch shape of the persistent
+ * batch kernel (threads {128, 256} x (spt 1, ring {16, 32}) or (spt 2, ring
+ * 16)) create this batch, time its graph with CUDA events on `stream` (best
+ * of three runs after one warm-up), and check that every tour's sum and
+ * infeasible count equal those of the first shape (CVRPSD_ERR_DEVICE_STATUS
+ * otherwise). The fastest shape becomes the context's configuration, so the
+ * next cvrpsd_batch_create uses it; result->best_dtype is the batch's own
+ * demand type. Arguments as for cvrpsd_batch_create. Synchronous.
+ */
+int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+                          int32_t demand_dtype, cvrpsd_tune_result *result, void *stream);
+
 /* One-shot batch: create, run on `stream`, read the results, destroy. */
 int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
                             int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible,

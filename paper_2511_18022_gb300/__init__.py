@@ -20,7 +20,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
     "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
-    "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
+    "cvrpsd_batch_create", "cvrpsd_batch_autotune", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
@@ -471,6 +471,18 @@ def cvrpsd_batch_create(ctx, tours, S: int) -> Batch:
     return Batch(ctx, tours, S)
 
 
+def cvrpsd_batch_autotune(ctx, tours, S: int, stream=None) -> dict:
+    """Time every launch shape of the batch kernel on these tours and keep the
+    fastest on the context (see include/cvrpsd.h); returns the chosen shape."""
+    arr, keep, dtype = _tour_descs(tours, S)
+    res = _lib.TuneResult()
+    _lib.check(ctx, _lib.load().cvrpsd_batch_autotune(ctx, len(tours), arr, int(S), int(dtype), ctypes.byref(res),
+                                                      _stream_ptr(stream)))
+    del keep
+    return {"threads": res.best.threads, "spt": res.best.spt, "ring": res.best.ring,
+            "ms": res.best_ms, "dtype": res.best_dtype, "shapes_timed": res.shapes_timed}
+
+
 def cvrpsd_batch_run(batch: Batch, stream=None) -> None:
     batch.run(stream)
 
@@ -541,6 +553,9 @@ class Splitter:
 
     def batch(self, tours, S) -> Batch:
         return Batch(self.ctx, tours, S)
+
+    def batch_autotune(self, tours, S, stream=None) -> dict:
+        return cvrpsd_batch_autotune(self.ctx, tours, S, stream)
 
     def split_batch(self, tours, S, stream=None) -> dict:
         return cvrpsd_split_eval_batch(self.ctx, tours, S, stream)

@@ -31,7 +31,7 @@ EXPORTS = [
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_gen_demand", "cvrpsd_set_profiling",
     "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
-    "cvrpsd_batch_destroy", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
+    "cvrpsd_batch_destroy", "cvrpsd_batch_autotune", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
     "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
     "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params",
@@ -117,6 +117,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_batch_run.argtypes = [vp, vp]
     lib.cvrpsd_batch_results.argtypes = [vp, vp, vp, vp, vp]
     lib.cvrpsd_batch_destroy.argtypes = [vp]
+    lib.cvrpsd_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, ctypes.POINTER(TuneResult), vp]
     lib.cvrpsd_split_eval_batch.argtypes = [vp, i32, ctypes.POINTER(TourDesc), i64, i32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)          # raises AttributeError if a symbol is missing

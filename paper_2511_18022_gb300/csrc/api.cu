@@ -902,6 +902,74 @@ int cvrpsd_batch_destroy(cvrpsd_batch *b)
     return CVRPSD_OK;
 }
 
+int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+                          int32_t demand_dtype, cvrpsd_tune_result *result, void *stream_ptr)
+{
+    if (!ctx || !result) return CVRPSD_ERR_ARG;
+    ctx->err[0] = 0;
+    if (T < 1) return fail(ctx, CVRPSD_ERR_ARG, "T = %d", T);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    const cvrpsd_config saved = ctx->cfg;
+    std::vector<int64_t> ref_sum((size_t)T), ref_inf((size_t)T), sum((size_t)T), inf((size_t)T);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaEventCreate(&ev[0]), "cudaEventCreate");
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(ctx, CVRPSD_ERR_CUDA, "cudaEventCreate");
+    }
+    cvrpsd_tune_result best{};
+    best.best_ms = 1e30f;
+    best.best_dtype = demand_dtype;
+    int rc = CVRPSD_OK;
+    bool have_ref = false;
+    static const DequeShape kShapes[] = {{128, 1, 16}, {128, 1, 32}, {128, 2, 16},
+                                         {256, 1, 16}, {256, 1, 32}, {256, 2, 16}};
+    for (const DequeShape &sh : kShapes) {
+        ctx->cfg = cvrpsd_config{CVRPSD_KERNEL_DEQUE, sh.threads, sh.spt, sh.ring};
+        cvrpsd_batch *b = nullptr;
+        rc = cvrpsd_batch_create(ctx, T, tours, S, demand_dtype, &b);
+        if (rc) break;
+        // the shape the batch actually runs (it may shrink to fit)
+        const cvrpsd_config ran{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring};
+        float t_best = 1e30f;
+        for (int rep = 0; rep < 4 && rc >= 0; ++rep) {
+            cudaEventRecord(ev[0], stream);
+            rc = cvrpsd_batch_run(b, stream);
+            cudaEventRecord(ev[1], stream);
+            if (rc >= 0) rc = cvrpsd_batch_results(b, sum.data(), inf.data(), nullptr, nullptr);
+            float ms = 0;
+            if (rc >= 0 && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && rep > 0 && ms < t_best)
+                t_best = ms;   // the first run warms up
+        }
+        cvrpsd_batch_destroy(b);
+        if (rc < 0) break;
+        if (!have_ref) {
+            ref_sum = sum;
+            ref_inf = inf;
+            have_ref = true;
+        } else if (sum != ref_sum || inf != ref_inf) {
+            rc = fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "batch shape %d/%d/%d changes a tour's result", sh.threads,
+                      sh.spt, sh.ring);
+            break;
+        }
+        ++best.shapes_timed;
+        if (t_best < best.best_ms) {
+            best.best_ms = t_best;
+            best.best = ran;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc < 0) {
+        ctx->cfg = saved;
+        return rc;
+    }
+    ctx->cfg = best.best;
+    *result = best;
+    return CVRPSD_OK;
+}
+
 int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
                             int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
                             int32_t *out_status, void *stream)

@@ -110,6 +110,28 @@ def test_batch_set_aside_and_one_shot(sp, cv):
     assert sp.stats()["overflow"] > 0
 
 
+@pytest.mark.parametrize("capped", [False, True])
+def test_batch_autotune(sp, cv, capped):
+    """The batch autotuner times every batch shape, checks that each gives the
+    same per-tour results, and leaves the fastest on the context; a batch
+    created afterwards uses it and still matches the oracle."""
+    S = 3000
+    insts, mats = mixed_tours(S, capped=capped)
+    tours = [dict(tour=i.tour, dist=i.dist, demand=dev(m), Q=i.Q, L=i.L) for i, m in zip(insts, mats)]
+    r = sp.batch_autotune(tours, S)
+    assert r["shapes_timed"] == 6 and r["ms"] > 0
+    assert (r["threads"], r["spt"], r["ring"]) in {(128, 1, 16), (128, 1, 32), (128, 2, 16),
+                                                   (256, 1, 16), (256, 1, 32), (256, 2, 16)}
+    b, tours, outs, res = run_batch(sp, insts, mats, S)
+    st = sp.stats()
+    assert (st["threads"], st["spt"], st["ring"]) == (r["threads"], r["spt"], r["ring"])
+    for k, (inst, m) in enumerate(zip(insts, mats)):
+        want, wsum, winf, _ = oracle.split_costs(inst.tour, inst.dist, m, inst.Q, inst.L, nthreads=8)
+        assert (res["sum"][k], res["infeasible"][k]) == (wsum, winf)
+        assert np.array_equal(outs[k].cpu().numpy(), want)
+    b.close()
+
+
 def test_batch_rejects_bad_tour(sp, cv):
     S = 64
     insts, mats = mixed_tours(S)
