@@ -374,6 +374,17 @@ int cvrpsd_surrogate_set_scale(cvrpsd_surrogate *sur, float len_mean, float len_
  * w3 [256], b3); *count receives the size. Synchronous. */
 int cvrpsd_surrogate_params(cvrpsd_surrogate *sur, float *h_get, const float *h_set, int64_t *count);
 
+/*
+ * Checkpoint of the surrogate trainer: a flat host blob of *bytes bytes
+ * (header: magic, version, n, parameter count, Adam step, tour-length scale;
+ * then the fp32 parameters and Adam's first and second moments). With h_get
+ * the current state is written there; with h_set the state is restored from
+ * a blob taken from a network of the same n (CVRPSD_ERR_ARG otherwise), so
+ * that training resumes where it stopped. Synchronous (waits for the device).
+ * An addition of this library: the paper trains no network.
+ */
+int cvrpsd_surrogate_state(cvrpsd_surrogate *sur, void *h_get, const void *h_set, int64_t *bytes);
+
 /* Largest S accepted by cvrpsd_split_eval_noalloc. */
 #define CVRPSD_NOALLOC_MAX_S 1048576
 

@@ -390,6 +390,34 @@ class Surrogate:
             self.handle, p.ctypes.data, None if src is None else src.ctypes.data, ctypes.byref(cnt)))
         return p
 
+    def state(self) -> bytes:
+        """Checkpoint of the trainer (parameters, Adam moments and step, input
+        scale) as bytes; see cvrpsd_surrogate_state."""
+        lib = _lib.load()
+        size = ctypes.c_int64(0)
+        _lib.check(self.ctx, lib.cvrpsd_surrogate_state(self.handle, None, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        _lib.check(self.ctx, lib.cvrpsd_surrogate_state(self.handle, buf, None, ctypes.byref(size)))
+        return buf.raw
+
+    def load_state(self, blob: bytes) -> None:
+        """Resume from a checkpoint taken by state() on a network of the same n."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        size = ctypes.c_int64(0)
+        lib = _lib.load()
+        _lib.check(self.ctx, lib.cvrpsd_surrogate_state(self.handle, None, None, ctypes.byref(size)))
+        if len(blob) != size.value:
+            raise CvrpsdError(_lib.ERR_ARG, f"checkpoint has {len(blob)} bytes, expected {size.value}")
+        _lib.check(self.ctx, lib.cvrpsd_surrogate_state(self.handle, None, buf, ctypes.byref(size)))
+
+    def save(self, path) -> None:
+        with open(path, "wb") as f:
+            f.write(self.state())
+
+    def load(self, path) -> None:
+        with open(path, "rb") as f:
+            self.load_state(f.read())
+
     def close(self):
         if self.handle is not None:
             _lib.load().cvrpsd_surrogate_destroy(self.handle)

@@ -34,7 +34,7 @@ EXPORTS = [
     "cvrpsd_batch_destroy", "cvrpsd_batch_autotune", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
     "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
-    "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params",
+    "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params", "cvrpsd_surrogate_state",
     "cvrpsd_surrogate_set_scale",
 ]
 SURROGATE_PARAMS = 67841
@@ -110,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_surrogate_train_step.argtypes = [vp, vp, i32, vp, ctypes.c_float, vp, vp]
     lib.cvrpsd_surrogate_gradients.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.cvrpsd_surrogate_params.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+    lib.cvrpsd_surrogate_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
     lib.cvrpsd_surrogate_set_scale.argtypes = [vp, ctypes.c_float, ctypes.c_float]
     lib.cvrpsd_autotune.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, ctypes.c_char_p,
                                     ctypes.POINTER(TuneResult), vp]

@@ -433,4 +433,58 @@ int cvrpsd_surrogate_params(cvrpsd_surrogate *s, float *h_get, const float *h_se
     return CVRPSD_OK;
 }
 
+// Layout of a surrogate checkpoint (host memory, native byte order).
+struct SurrogateStateHeader {
+    uint32_t magic;       // kSurrogateStateMagic
+    uint32_t version;     // 1
+    int32_t n;            // customers of the instance the network was built for
+    int32_t params;       // kMlpParams
+    int32_t step;         // Adam steps taken
+    float len_mean;       // tour-length input scale
+    float len_inv_sd;
+    int32_t reserved;
+};
+constexpr uint32_t kSurrogateStateMagic = 0x53504443u;
+
+int cvrpsd_surrogate_state(cvrpsd_surrogate *s, void *h_get, const void *h_set, int64_t *bytes)
+{
+    if (!s) return CVRPSD_ERR_ARG;
+    cvrpsd_ctx *ctx = s->ctx;
+    const size_t arr = sizeof(float) * (size_t)kMlpParams;
+    const size_t total = sizeof(SurrogateStateHeader) + 3 * arr;
+    if (bytes) *bytes = (int64_t)total;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (h_set) {
+        SurrogateStateHeader h;
+        memcpy(&h, h_set, sizeof(h));
+        if (h.magic != kSurrogateStateMagic || h.version != 1)
+            return fail(ctx, CVRPSD_ERR_ARG, "not a surrogate checkpoint (magic %08x, version %u)", h.magic, h.version);
+        if (h.n != s->n || h.params != kMlpParams)
+            return fail(ctx, CVRPSD_ERR_ARG, "checkpoint of a network for n = %d (%d parameters), this one has n = %d",
+                        h.n, h.params, s->n);
+        if (h.step < 0 || !(h.len_inv_sd > 0.0f))
+            return fail(ctx, CVRPSD_ERR_ARG, "checkpoint header out of range");
+        const char *src = static_cast<const char *>(h_set) + sizeof(h);
+        CK(cudaMemcpy(s->d_p, src, arr, cudaMemcpyHostToDevice), "restore parameters");
+        CK(cudaMemcpy(s->d_m, src + arr, arr, cudaMemcpyHostToDevice), "restore first moments");
+        CK(cudaMemcpy(s->d_v, src + 2 * arr, arr, cudaMemcpyHostToDevice), "restore second moments");
+        CK(mlp_to_bf16(s->d_p, s->d_pb, nullptr), "bf16 copy");
+        CK(cudaDeviceSynchronize(), "synchronize");
+        s->step = h.step;
+        s->len_mean = h.len_mean;
+        s->len_inv_sd = h.len_inv_sd;
+    }
+    if (h_get) {
+        CK(cudaDeviceSynchronize(), "synchronize");
+        SurrogateStateHeader h{kSurrogateStateMagic, 1u, s->n, (int32_t)kMlpParams, s->step, s->len_mean,
+                               s->len_inv_sd, 0};
+        char *dst = static_cast<char *>(h_get);
+        memcpy(dst, &h, sizeof(h));
+        CK(cudaMemcpy(dst + sizeof(h), s->d_p, arr, cudaMemcpyDeviceToHost), "save parameters");
+        CK(cudaMemcpy(dst + sizeof(h) + arr, s->d_m, arr, cudaMemcpyDeviceToHost), "save first moments");
+        CK(cudaMemcpy(dst + sizeof(h) + 2 * arr, s->d_v, arr, cudaMemcpyDeviceToHost), "save second moments");
+    }
+    return CVRPSD_OK;
+}
+
 }  // extern "C"

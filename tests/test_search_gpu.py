@@ -139,6 +139,41 @@ def test_surrogate_gradients_match_reference(sp, cv):
     sur.close()
 
 
+def test_surrogate_checkpoint_resume(sp, cv, tmp_path):
+    """A checkpoint restores parameters, Adam moments, step and input scale
+    exactly, and training resumed from it follows the uninterrupted run."""
+    inst, cust, sur, tours, target = surrogate_case(cv, sp, T=256, seed=4)
+    sur.set_scale(20000.0, 900.0)
+    dT, dY = torch.from_numpy(tours).cuda(), torch.from_numpy(target).cuda()
+    for _ in range(3):
+        sur.train_step(dT, dY, 1e-3)
+    path = tmp_path / "sur.ckpt"
+    sur.save(path)
+    blob = path.read_bytes()
+    other = cv.Surrogate(sp.ctx, cust, inst.dist, Q=64.0, seed=99)     # different initial weights
+    assert not np.array_equal(other.params(), sur.params())
+    other.load(path)
+    assert other.state() == blob                                        # exact restore
+    assert np.array_equal(other.params(), sur.params())
+    for _ in range(4):
+        sur.train_step(dT, dY, 1e-3)
+        other.train_step(dT, dY, 1e-3)
+    a, b = sur.params(), other.params()
+    ckpt = np.frombuffer(blob, dtype=np.float32, count=M.NPARAMS, offset=32)
+    assert np.abs(a - ckpt).max() > 1e-4                                # training moved on
+    # the two runs differ only by the order of floating-point atomics in the
+    # gradient sums: almost all parameters agree to rounding, and no update
+    # can differ by more than Adam's step bound (lr per step)
+    d = np.abs(a - b)
+    assert np.percentile(d, 99) <= 1e-6 and d.max() <= 2 * 4 * 1e-3
+    # a checkpoint of a network for another n is refused
+    inst2, cust2, sur2, _, _ = surrogate_case(cv, sp, n=23, T=8, seed=6)
+    with pytest.raises(cv.CvrpsdError):
+        sur2.load_state(blob)
+    for s in (sur, other, sur2):
+        s.close()
+
+
 def test_training_reduces_loss(sp, cv):
     inst, cust, sur, tours, _ = surrogate_case(cv, sp, T=512, seed=5)
     dT = torch.from_numpy(tours).cuda()
