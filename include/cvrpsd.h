@@ -123,6 +123,13 @@ int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats);
  * durations in cvrpsd_stats. Off by default. */
 int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on);
 
+/* Test hook for the error paths: after `after` more device or pinned-host
+ * allocations made for `ctx` (its scratch, batches, surrogates), the next one
+ * fails as if memory had run out (the call returns CVRPSD_ERR_NOMEM and
+ * leaves the context usable); after < 0 turns the hook off. The hook fires
+ * once. Not for production use. */
+int cvrpsd_debug_fail_alloc(cvrpsd_ctx *ctx, int32_t after);
+
 /*
  * Split one giant tour under S scenarios (Section 3, Eq. 1-3) and reduce the
  * costs to the sample-average of Appendix A.

@@ -105,19 +105,19 @@ int check_host_buffer(cvrpsd_ctx *ctx, const void *ptr, unsigned long long bytes
 
 int ensure_scratch(cvrpsd_ctx *ctx, long long S)
 {
-    if (!ctx->d_acc) {
-        CK(cudaMalloc(&ctx->d_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMalloc(acc)");
-        CK(cudaMallocHost(&ctx->h_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMallocHost(acc)");
-        CK(cudaMalloc(&ctx->d_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMalloc(tab)");
-        CK(cudaMallocHost(&ctx->h_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMallocHost(tab)");
-        CK(cudaEventCreateWithFlags(&ctx->ev_tab, cudaEventDisableTiming), "cudaEventCreate");
-    }
+    // Each resource on its own: after a failed allocation the next call
+    // retries only what is still missing.
+    if (!ctx->d_acc) CK(dev_alloc(ctx, &ctx->d_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMalloc(acc)");
+    if (!ctx->h_acc) CK(host_alloc(ctx, &ctx->h_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMallocHost(acc)");
+    if (!ctx->d_tab) CK(dev_alloc(ctx, &ctx->d_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMalloc(tab)");
+    if (!ctx->h_tab) CK(host_alloc(ctx, &ctx->h_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMallocHost(tab)");
+    if (!ctx->ev_tab) CK(cudaEventCreateWithFlags(&ctx->ev_tab, cudaEventDisableTiming), "cudaEventCreate");
     if (S > ctx->list_cap) {
         if (ctx->d_list) cudaFree(ctx->d_list);
         ctx->d_list = nullptr;
         ctx->list_cap = 0;
         long long cap = S < 4096 ? 4096 : S;
-        cudaError_t e = cudaMalloc(&ctx->d_list, (size_t)cap * sizeof(int32_t));
+        cudaError_t e = dev_alloc(ctx, &ctx->d_list, (size_t)cap * sizeof(int32_t));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, CVRPSD_ERR_NOMEM, "overflow list of %lld entries: %s", cap, cudaGetErrorString(e));
@@ -244,6 +244,13 @@ int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats)
     return CVRPSD_OK;
 }
 
+int cvrpsd_debug_fail_alloc(cvrpsd_ctx *ctx, int32_t after)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    ctx->fail_alloc_after = after < 0 ? -1 : after;
+    return CVRPSD_OK;
+}
+
 int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on)
 {
     if (!ctx) return CVRPSD_ERR_ARG;
@@ -354,7 +361,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
                 if (*buf) cudaFree(*buf);
                 *buf = nullptr;
                 *cap = 0;
-                if (cudaMalloc(buf, sizeof(int32_t) * need) != cudaSuccess) {
+                if (dev_alloc(ctx, buf, sizeof(int32_t) * need) != cudaSuccess) {
                     cudaGetLastError();
                     rc2 = fail(ctx, CVRPSD_ERR_NOMEM, "%s", what);
                     return;
@@ -627,8 +634,9 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     void *tmp[2] = {nullptr, nullptr};
     unsigned int *sat = nullptr;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
-    if (cudaMalloc(&tmp[0], (size_t)n * Ss * 2) == cudaSuccess && cudaMalloc(&tmp[1], (size_t)n * Ss * 4) == cudaSuccess &&
-        cudaMalloc(&sat, sizeof(unsigned int)) == cudaSuccess && cudaMemsetAsync(sat, 0, 4, stream) == cudaSuccess &&
+    if (dev_alloc(ctx, &tmp[0], (size_t)n * Ss * 2) == cudaSuccess &&
+        dev_alloc(ctx, &tmp[1], (size_t)n * Ss * 4) == cudaSuccess &&
+        dev_alloc(ctx, &sat, sizeof(unsigned int)) == cudaSuccess && cudaMemsetAsync(sat, 0, 4, stream) == cudaSuccess &&
         launch_convert_demand(demand, demand_dtype, ld, tmp[0], 2, Ss, n, Ss, sat, stream) == cudaSuccess &&
         launch_convert_demand(demand, demand_dtype, ld, tmp[1], 4, Ss, n, Ss, sat, stream) == cudaSuccess) {
         unsigned int h_sat = 1;
@@ -800,12 +808,12 @@ int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tour
     b->acc_words = BACC_WORDS + 3 * (size_t)T;
     const long long list_cap = std::min<long long>((long long)T * S, 1LL << 24);
 #define BK(call, what)                              do {                                                cudaError_t e_ = (call);                        if (e_ != cudaSuccess) {                            int rc_ = cuda_fail(ctx, e_, what);             cudaGetLastError();                             batch_free(b);                                  return rc_;                                 }                                           } while (0)
-    BK(cudaMalloc(&b->d_tours, sizeof(TourDev) * T), "cudaMalloc(tours)");
-    BK(cudaMalloc(&b->d_tabs, sizeof(TourStep) * total_n), "cudaMalloc(tables)");
-    BK(cudaMalloc(&b->d_items, sizeof(int2) * items.size()), "cudaMalloc(items)");
-    BK(cudaMalloc(&b->d_acc, sizeof(unsigned long long) * b->acc_words), "cudaMalloc(acc)");
-    BK(cudaMalloc(&b->d_list, sizeof(int2) * list_cap), "cudaMalloc(list)");
-    BK(cudaMallocHost(&b->h_acc, sizeof(unsigned long long) * b->acc_words), "cudaMallocHost(acc)");
+    BK(dev_alloc(ctx, &b->d_tours, sizeof(TourDev) * T), "cudaMalloc(tours)");
+    BK(dev_alloc(ctx, &b->d_tabs, sizeof(TourStep) * total_n), "cudaMalloc(tables)");
+    BK(dev_alloc(ctx, &b->d_items, sizeof(int2) * items.size()), "cudaMalloc(items)");
+    BK(dev_alloc(ctx, &b->d_acc, sizeof(unsigned long long) * b->acc_words), "cudaMalloc(acc)");
+    BK(dev_alloc(ctx, &b->d_list, sizeof(int2) * list_cap), "cudaMalloc(list)");
+    BK(host_alloc(ctx, &b->h_acc, sizeof(unsigned long long) * b->acc_words), "cudaMallocHost(acc)");
     for (int t = 0; t < T; ++t) hd[t].tab = b->d_tabs + tab_off[t];
     BK(cudaMemcpy(b->d_tours, hd.data(), sizeof(TourDev) * T, cudaMemcpyHostToDevice), "upload tours");
     BK(cudaMemcpy(b->d_tabs, htab.data(), sizeof(TourStep) * total_n, cudaMemcpyHostToDevice), "upload tables");
@@ -1005,11 +1013,9 @@ int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind, const int32_
     if (S == 0) return CVRPSD_OK;
     int rc = check_device_buffer(ctx, out, ((unsigned long long)(n - 1) * ld + S) * dtype, "out");
     if (rc) return rc;
-    if (!ctx->d_gen) {
-        CK(cudaMalloc(&ctx->d_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMalloc(gen)");
-        CK(cudaMallocHost(&ctx->h_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMallocHost(gen)");
-        CK(cudaEventCreateWithFlags(&ctx->ev_gen, cudaEventDisableTiming), "cudaEventCreate");
-    }
+    if (!ctx->d_gen) CK(dev_alloc(ctx, &ctx->d_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMalloc(gen)");
+    if (!ctx->h_gen) CK(host_alloc(ctx, &ctx->h_gen, 2 * (CVRPSD_MAX_N + 1) * sizeof(int32_t)), "cudaMallocHost(gen)");
+    if (!ctx->ev_gen) CK(cudaEventCreateWithFlags(&ctx->ev_gen, cudaEventDisableTiming), "cudaEventCreate");
     CK(cudaEventSynchronize(ctx->ev_gen), "cudaEventSynchronize");
     for (int k = 0; k < n; ++k) {
         ctx->h_gen[k] = mu[k];

@@ -49,6 +49,8 @@ struct cvrpsd_ctx {
     long long seq_flags_cap = 0;
     int32_t *seq_mats = nullptr;
     long long seq_mats_cap = 0;
+    // test hook (cvrpsd_debug_fail_alloc): allocations left before one fails; -1 = off
+    int fail_alloc_after = -1;
 };
 
 namespace cvrpsd {
@@ -66,7 +68,39 @@ inline int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
 
 inline int cuda_fail(cvrpsd_ctx *ctx, cudaError_t e, const char *what)
 {
-    return fail(ctx, CVRPSD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ctx, e == cudaErrorMemoryAllocation ? CVRPSD_ERR_NOMEM : CVRPSD_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Every device and pinned-host allocation of a context goes through these, so
+// that the test hook can make one of them fail as if memory had run out.
+inline bool injected_alloc_failure(cvrpsd_ctx *ctx)
+{
+    if (!ctx || ctx->fail_alloc_after < 0) return false;
+    if (ctx->fail_alloc_after == 0) {
+        ctx->fail_alloc_after = -1;
+        return true;
+    }
+    --ctx->fail_alloc_after;
+    return false;
+}
+template <typename T>
+inline cudaError_t dev_alloc(cvrpsd_ctx *ctx, T **p, size_t bytes)
+{
+    if (injected_alloc_failure(ctx)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+inline cudaError_t host_alloc(cvrpsd_ctx *ctx, T **p, size_t bytes)
+{
+    if (injected_alloc_failure(ctx)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(reinterpret_cast<void **>(p), bytes);
 }
 
 }  // namespace cvrpsd

@@ -33,7 +33,7 @@ int grow(cvrpsd_ctx *ctx, T **buf, long long *cap, long long need, const char *w
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(buf, sizeof(T) * (size_t)need);
+    cudaError_t e = dev_alloc(ctx, buf, sizeof(T) * (size_t)need);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, CVRPSD_ERR_NOMEM, "%s (%lld entries): %s", what, need, cudaGetErrorString(e));
@@ -217,16 +217,19 @@ int sur_workspace(cvrpsd_surrogate *s, long long T)
 {
     cvrpsd_ctx *ctx = s->ctx;
     if (T <= s->cap) return CVRPSD_OK;
+    // The old buffers go first; until all new ones exist the capacity is 0,
+    // so a failed call leaves nothing that a later call could mistake for room.
+    s->cap = 0;
     for (float **p : {&s->d_zt, &s->d_U, &s->d_y, &s->d_dy, &s->d_dU, &s->d_dzt}) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
-    CK(cudaMalloc(&s->d_zt, sizeof(float) * T * kMlpIn2), "surrogate workspace");
-    CK(cudaMalloc(&s->d_U, sizeof(float) * T * kMlpH), "surrogate workspace");
-    CK(cudaMalloc(&s->d_y, sizeof(float) * T), "surrogate workspace");
-    CK(cudaMalloc(&s->d_dy, sizeof(float) * T), "surrogate workspace");
-    CK(cudaMalloc(&s->d_dU, sizeof(float) * T * kMlpH), "surrogate workspace");
-    CK(cudaMalloc(&s->d_dzt, sizeof(float) * T * kMlpIn2), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_zt, sizeof(float) * T * kMlpIn2), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_U, sizeof(float) * T * kMlpH), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_y, sizeof(float) * T), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_dy, sizeof(float) * T), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_dU, sizeof(float) * T * kMlpH), "surrogate workspace");
+    CK(dev_alloc(ctx, &s->d_dzt, sizeof(float) * T * kMlpIn2), "surrogate workspace");
     s->cap = T;
     return CVRPSD_OK;
 }
@@ -324,14 +327,14 @@ int cvrpsd_surrogate_create(cvrpsd_ctx *ctx, int32_t n, const float *cust, const
             return cuda_fail(ctx, e_, what);    \
         }                                       \
     } while (0)
-    SK(cudaMalloc(&s->d_cust, sizeof(float) * n * 4), "cudaMalloc");
-    SK(cudaMalloc(&s->d_dist, sizeof(int32_t) * N1 * N1), "cudaMalloc");
-    SK(cudaMalloc(&s->d_p, sizeof(float) * kMlpParams), "cudaMalloc");
-    SK(cudaMalloc(&s->d_g, sizeof(float) * kMlpParams), "cudaMalloc");
-    SK(cudaMalloc(&s->d_m, sizeof(float) * kMlpParams), "cudaMalloc");
-    SK(cudaMalloc(&s->d_v, sizeof(float) * kMlpParams), "cudaMalloc");
-    SK(cudaMalloc(&s->d_pb, sizeof(__nv_bfloat16) * kMlpParams), "cudaMalloc");
-    SK(cudaMalloc(&s->d_loss, sizeof(float)), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_cust, sizeof(float) * n * 4), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_dist, sizeof(int32_t) * N1 * N1), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_p, sizeof(float) * kMlpParams), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_g, sizeof(float) * kMlpParams), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_m, sizeof(float) * kMlpParams), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_v, sizeof(float) * kMlpParams), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_pb, sizeof(__nv_bfloat16) * kMlpParams), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_loss, sizeof(float)), "cudaMalloc");
     SK(cudaMemcpy(s->d_cust, c.data(), sizeof(float) * n * 4, cudaMemcpyHostToDevice), "upload");
     SK(cudaMemcpy(s->d_dist, dist, sizeof(int32_t) * N1 * N1, cudaMemcpyHostToDevice), "upload");
     SK(cudaMemcpy(s->d_p, p.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice), "upload");
