@@ -208,20 +208,26 @@ def train_surrogate(sur: Surrogate, tours, costs, *, dist=None, epochs: int = 8,
     return (mean, sd), mae
 
 
-def oos_study(ctx, inst, D_train, D_test, S_list, *, iterations: int = 400, seed: int = 0, k: int = 64):
+def oos_study(ctx, inst, D_train, D_test, S_list, *, iterations: int = 400, seed: int = 0, k: int = 64,
+              repeats: int = 1):
     """Out-of-sample effect of the scenario count (the study of Section 4.2
     on a synthetic instance): for each S in S_list, local search with the
-    exact Split on the first S training scenarios, from one common start;
-    the final tour is then split under the held-out scenarios D_test.
-    Returns rows (S, in-sample SAA cost, out-of-sample SAA cost)."""
-    import torch
-    start = np.random.default_rng(seed).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    exact Split on the first S training scenarios; the final tour is then
+    split under the held-out scenarios D_test. With repeats > 1 every S runs
+    that many searches (start and move seeds seed, seed+1, ...) and the row
+    holds the means. Returns rows (S, in-sample SAA cost, out-of-sample SAA
+    cost)."""
     test_eval = Evaluator(ctx, inst, D_test)
     rows = []
     for S in S_list:
         Dtr = D_train[:, :S].contiguous()
-        ls = LocalSearch(ctx, inst, Dtr, start, k=k, seed=seed + 1)
-        ls.run(iterations)
-        oos = float(test_eval(ls.cur.view(1, -1))[0].item())
-        rows.append((int(S), ls.cur_cost, oos))
+        ins, outs = [], []
+        for r in range(repeats):
+            sd = seed + 1000 * r
+            start = np.random.default_rng(sd).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+            ls = LocalSearch(ctx, inst, Dtr, start, k=k, seed=sd + 1)
+            ls.run(iterations)
+            ins.append(ls.cur_cost)
+            outs.append(float(test_eval(ls.cur.view(1, -1))[0].item()))
+        rows.append((int(S), float(np.mean(ins)), float(np.mean(outs))))
     return rows
