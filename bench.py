@@ -277,13 +277,13 @@ def run_ours(args):
     algo_bytes = n * S * 2 + S * 4 + n * 8
     peak, peak_kind = peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
-    traffic, inst = None, None
+    traffic, winst = None, None
     shape = f"{st['threads']},{st['spt']},{st['ring']}"
     try:
         t = json.load(open(TRAFFIC_FILE))
         if t.get("kernel_hash") == kernel_hash() and S == (1 << 20):
             traffic = t["shapes"].get(shape)
-            inst = t.get("inst_executed", {}).get(shape)
+            winst = t.get("inst_executed", {}).get(shape)
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -293,14 +293,14 @@ def run_ours(args):
     # The kernel is bound by instruction issue: warp instructions per launch
     # (ncu, same kernel source and shape) against one instruction per clock per
     # scheduler, 4 schedulers per SM, at the SM clock sampled in the timed region.
-    if inst and clk.get("sm_mhz"):
+    if winst and clk.get("sm_mhz"):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         ipeak = sms * 4 * clk["sm_mhz"] * 1e6
-        iach = inst / (kernel_ms / 1e3)
+        iach = winst / (kernel_ms / 1e3)
         roofline["issue"] = {"achieved": round(iach / 1e9, 1), "peak": round(ipeak / 1e9, 1),
                              "unit": "G warp-instructions/s", "frac": round(iach / ipeak, 4),
-                             "warp_instructions_per_launch": inst,
-                             "per_warp_position": round(inst / (S / 32 * n), 2)}
+                             "warp_instructions_per_launch": winst,
+                             "per_warp_position": round(winst / (S / 32 * n), 2)}
 
     # end to end from pinned host memory
     if args.e2e_steps > 0:
