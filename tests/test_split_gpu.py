@@ -3,6 +3,9 @@
 Every comparison is element by element and bit-exact: costs are integers.
 Inputs come from the seeded host generators in synth/ and are copied to the
 device; the oracle never sees anything the CUDA path produced."""
+import dataclasses
+import functools
+
 import numpy as np
 import pytest
 
@@ -169,6 +172,26 @@ def test_all_infeasible(sp):
     r, got = check_parity(sp, inst, D)
     assert r.infeasible == 64 and np.isnan(r.mean) and (got == INT32_MAX).all()
     assert r.status == 1
+
+
+@functools.lru_cache(maxsize=1)
+def largest_case(n):
+    inst = make_instance(n, 5, 30, seed=31, Q=150)
+    return inst, demand_matrix(inst.mu, inst.region, 1, 17, 640, dtype=np.int16)
+
+
+@pytest.mark.parametrize("kernel, L", [("deque", None), ("deque", 40), ("warp", 40), ("seqpar", None)])
+def test_largest_tour(sp, cv, kernel, L):
+    """n = CVRPSD_MAX_N customers: every kernel at the library's size limit
+    (the table, the key scale, the warp kernel's per-warp prefix loads and
+    the sequence-parallel matrices all at their largest)."""
+    inst0, D0 = largest_case(cv.MAX_N)
+    inst = inst0 if L is None else dataclasses.replace(inst0, L=L)
+    D = D0[:, :64] if kernel == "seqpar" else D0
+    code = {"deque": cv.KERNEL_DEQUE, "warp": cv.KERNEL_WARP, "seqpar": cv.KERNEL_SEQPAR}[kernel]
+    sp.configure(kernel=code)
+    check_parity(sp, inst, D)
+    assert sp.stats()["kernel"] == code
 
 
 def test_deque_overflow_goes_to_warp_kernel(sp, cv):
