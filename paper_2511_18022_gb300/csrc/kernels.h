@@ -96,10 +96,10 @@ struct BatchParams {
     int max_n;                    // largest tour
 };
 
+// Dynamic shared memory of the batch kernel: rings, then the current tour's table.
 inline size_t split_batch_smem(int max_n, const DequeShape &shape)
 {
-    (void)max_n;   // the tour tables are read from global memory
-    return (size_t)shape.spt * shape.ring * shape.threads * 8;
+    return (size_t)shape.spt * shape.ring * shape.threads * 8 + (size_t)max_n * sizeof(TourStep);
 }
 // Persistent deque kernel over all work items; with configure_only it only
 // sets the kernel's shared-memory limit (call before stream capture) and

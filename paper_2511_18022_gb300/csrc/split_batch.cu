@@ -1,9 +1,10 @@
 // Batched Split: many giant tours, each with its own scenario matrix, in one
 // persistent launch. Blocks take work items (tour, tile of T * SPT
 // scenarios) from an atomic counter in the order the host chose (largest
-// tours first) and walk the tile exactly as the single-tour kernel does,
-// reading the tour's table from global memory. Each block adds its tile's
-// cost sum to the tour's accumulator.
+// tours first), copy the tour's table into shared memory when the tour
+// changes (blocks hop between tours, so a shared copy beats L1 here), and
+// walk the tile exactly as the single-tour kernel does. Each block adds its
+// tile's cost sum to the tour's accumulator.
 #include "split_deque.cuh"
 
 namespace cvrpsd {
@@ -15,8 +16,12 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
     __shared__ int s_item;
     __shared__ long long s_sum[T / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);   // the rings
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     unsigned long long *tacc = b.acc + BACC_WORDS;
+    // the current tour's table follows the rings
+    TourStep *tabp = reinterpret_cast<TourStep *>(smem + (size_t)SPT * R * T * 8);
+    const uint32_t tab_s = sbase + (uint32_t)SPT * R * T * 8;
+    int cur = -1;
     for (;;) {
         __syncthreads();                          // the previous item is finished everywhere
         if (tid == 0) s_item = (int)atomicAdd(reinterpret_cast<unsigned int *>(b.acc + BACC_COUNTER), 1u);
@@ -26,12 +31,18 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
         const int2 it = b.items ? b.items[item] : make_int2(item / b.tiles, item % b.tiles);
         const TourDev td = b.tours[it.x];
         const int t = it.x;
+        if (t != cur) {   // block-uniform; the loop-top barrier has retired the previous item
+            for (int k = tid; k < td.n; k += T) tabp[k] = td.tab[k];
+            __syncthreads();
+            cur = t;
+        }
+        const TabShared tabref{tab_s};
         const long long s_first = ((long long)it.y * T + tid) * SPT;
         unsigned long long *acc = b.acc;
         int2 *list = b.list;
         const long long cap = b.list_cap;
         long long sum = split_thread<DT, SPT, R, T, LCAP>(
-            td.demand, td.ld, b.S, s_first, td.n, td.Q, td.L, td.K, td.g0, sbase, TabGlobal{reinterpret_cast<const int *>(td.tab)}, tid, td.out_cost,
+            td.demand, td.ld, b.S, s_first, td.n, td.Q, td.L, td.K, td.g0, sbase, tabref, tid, td.out_cost,
             [acc, list, cap, t](long long s) {
                 const unsigned long long idx = atomicAdd(acc + BACC_LIST, 1ull);
                 if ((long long)idx < cap) list[idx] = make_int2(t, (int)s);

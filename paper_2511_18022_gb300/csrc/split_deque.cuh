@@ -95,10 +95,18 @@ __device__ __forceinline__ void sts2(uint32_t a, int x, int y)
     asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y) : "memory");
 }
 
-// Tour table (TourStep = {row, c}, entry i-1 for position i), read straight
-// from global memory with read-only loads. Every lane of a block reads the
-// same entry (all threads walk the same tour position), so a read is one L1
-// broadcast, and shared memory is left to the rings.
+// Tour table (TourStep = {row, c}, entry i-1 for position i) as the walk
+// reads it. Every lane of a block reads the same entry (all threads walk the
+// same tour position), so either way a read is one broadcast.
+// TabGlobal: straight from global memory with read-only loads (the
+// single-tour kernel: the table stays in L1 and shared memory is left to the
+// rings). TabShared: from a copy in shared memory (the batch kernel, whose
+// blocks move between tours).
+struct TabShared {
+    uint32_t a;   // shared-window address of entry 0
+    __device__ __forceinline__ int row(int i) const { return lds1(a + (uint32_t)(i - 1) * 8u); }
+    __device__ __forceinline__ int c(int i) const { return lds1(a + (uint32_t)(i - 1) * 8u + 4u); }
+};
 struct TabGlobal {
     const int *p;   // entry 0 as two ints (row, c)
     __device__ __forceinline__ int row(int i) const { return __ldg(p + 2 * (i - 1)); }
@@ -280,7 +288,7 @@ __device__ __forceinline__ void prefetch_block(const char *base, const TB &tab, 
 }
 
 // The walk of one thread: SPT adjacent scenarios s_first.. of one tour whose
-// table is read through `tab` (TabGlobal); the rings start at
+// table is read through `tab` (TabGlobal or TabShared); the rings start at
 // shared address `rings`. Writes f(n) of feasible scenarios to out_cost (if
 // given), returns the sum of those costs, and passes every scenario it sets
 // aside to `set_aside(s)`. Threads with no scenario (s_first >= S) walk
