@@ -65,7 +65,7 @@ extern "C" {
 #define CVRPSD_MAX_N 8191
 
 /* Kernel choice for the Split (see cvrpsd_config). AUTO takes SEQPAR for
- * S <= 64 scenarios on tours of n >= 128 (lowest latency there) and DEQUE
+ * S <= 256 scenarios on tours of n >= 128 (lowest latency there) and DEQUE
  * otherwise. */
 #define CVRPSD_KERNEL_AUTO   0
 #define CVRPSD_KERNEL_DEQUE  1   /* one thread per scenario, monotone deque */

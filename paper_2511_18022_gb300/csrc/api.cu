@@ -350,7 +350,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
         // along the tour); otherwise scenario parallelism wins.
         int kernel = ctx->cfg.kernel;
         if (kernel == CVRPSD_KERNEL_AUTO)
-            kernel = (S <= 64 && n >= 128 && !pred) ? CVRPSD_KERNEL_SEQPAR : CVRPSD_KERNEL_DEQUE;
+            kernel = (S <= 256 && n >= 128 && !pred) ? CVRPSD_KERNEL_SEQPAR : CVRPSD_KERNEL_DEQUE;
         const int warp_grid = 2 * (ctx->sm_count > 0 ? ctx->sm_count : 152);
         if (kernel == CVRPSD_KERNEL_SEQPAR && !pred) {
             if (S > 4096) return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "the sequence-parallel kernel takes S <= 4096");

@@ -97,15 +97,36 @@ __global__ void __launch_bounds__(kSeqW) seqpar_block_kernel(SeqParParams a)
         head = (head - 1) & (kSeqW - 1);           // shift: old rows move down by one
         Mx[head][j] = row0;
     }
+    // Stored transposed, out[c * kSeqW + r] = M[r][c], so that the fold reads
+    // it with unit stride; thread j writes element j of every stored row
+    // (coalesced), reading row j of M from the other threads' columns.
+    __syncthreads();
     int *out = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
-    for (int r = 0; r < kSeqW; ++r) out[r * kSeqW + j] = Mx[(head + r) & (kSeqW - 1)][j];
+    const int slot = (head + j) & (kSeqW - 1);
+    for (int c = 0; c < kSeqW; ++c) out[c * kSeqW + j] = Mx[slot][c];
 }
 
-// Fold the block matrices over x_0 and write f(n); one warp pair per scenario.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Fold the block matrices over x_0 and write f(n); one warp pair per
+// scenario. Each (transposed) matrix is copied into shared memory with async
+// copies one block ahead of its use, so the mat-vec reads shared memory only.
 __global__ void __launch_bounds__(kSeqW) seqpar_fold_kernel(SeqParParams a)
 {
     __shared__ int x[kSeqW];
-    __shared__ long long s_sum;
+    __shared__ __align__(16) int Mt[2][kSeqW * kSeqW];
     const int s = blockIdx.x, r = threadIdx.x;
     if (s >= a.S) return;
     if (a.flags[s]) {                              // handed to the warp kernel
@@ -116,15 +137,29 @@ __global__ void __launch_bounds__(kSeqW) seqpar_fold_kernel(SeqParParams a)
         return;
     }
     x[r] = r == 0 ? a.g0 : kInf;
-    __syncthreads();
-    for (int b = 0; b < a.blocks; ++b) {
+    auto load = [&](int b) {   // 16-byte chunks of matrix b, linear and coalesced
         const int *M = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&Mt[b & 1][0]);
+        for (int k = r; k < kSeqW * kSeqW / 4; k += kSeqW) cp_async16(dst + 16u * k, M + 4 * k);
+        cp_async_commit();
+    };
+    load(0);
+    for (int b = 0; b < a.blocks; ++b) {
+        if (b + 1 < a.blocks) {
+            load(b + 1);
+            cp_async_wait<1>();    // matrix b has landed (this thread's part)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();           // every thread's part of matrix b, and x
+        const int *M = Mt[b & 1];
         int v = kInf;
-        for (int c = 0; c < kSeqW; ++c) v = min(v, sat_add(M[r * kSeqW + c], x[c]));
-        __syncthreads();
+#pragma unroll 16
+        for (int c = 0; c < kSeqW; ++c) v = min(v, sat_add(M[c * kSeqW + r], x[c]));
+        __syncthreads();           // all reads of x and of this buffer are done
         x[r] = v;
-        __syncthreads();
     }
+    __syncthreads();
     if (r == 0) {
         const int cost = x[0];
         if (a.out_cost) a.out_cost[s] = cost;
