@@ -540,6 +540,61 @@ def run_oos(args):
     return 0
 
 
+def run_latency(args):
+    """latency-n1000: device time of one Split call of the n = 1000 tour for
+    few scenarios, per kernel (deque, warp, sequence-parallel): the regime
+    where scenario parallelism cannot fill the GPU."""
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2511_18022_gb300 as cv
+    from paper_2511_18022_gb300 import build
+    from synth import workload
+
+    build.build()
+    w = workload("million-n1000", S=4096)
+    inst = w.instances[0]
+    sp = cv.Splitter(local)
+    D = torch.empty((inst.n, 4096), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    sp.profiling(True)
+    kernels = (("deque", cv.KERNEL_DEQUE), ("warp", cv.KERNEL_WARP), ("seqpar", cv.KERNEL_SEQPAR))
+    rows, launches = [], 0
+    for S in (1, 8, 64, 512, 4096):
+        row = {"S": S}
+        sums = set()
+        for name, k in kernels:
+            sp.configure(kernel=k)
+            for _ in range(max(args.warmup, 1)):
+                sp.split(inst.tour, inst.dist, D, inst.Q, inst.L, S=S)
+            ms = []
+            for _ in range(args.steps):
+                r = sp.split(inst.tour, inst.dist, D, inst.Q, inst.L, S=S)
+                st = sp.stats()
+                ms.append(st["kernel_ms"] + max(st["fallback_ms"], 0.0))
+                launches += st["launches"]
+                sums.add(r.sum)
+            row[name + "_ms"] = float(np.median(ms))
+        assert len(sums) == 1, "kernels disagree"
+        rows.append(row)
+    sp.configure(kernel=cv.KERNEL_AUTO)
+    if rank == 0:
+        best = rows[0]["seqpar_ms"]
+        print(json.dumps({
+            "metric": "device time of one Split call, n=1000, S=1 (sequence-parallel kernel)", "value": best,
+            "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": "latency-n1000", "n": inst.n, "Q": inst.Q, "L": inst.L,
+                       "timing": "CUDA events of the library around its kernels, median per call"},
+            "rows": rows, "gpu_launches": launches,
+        }))
+    sp.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,6 +625,8 @@ def main():
         return run_batched(args)
     if args.workload == "surrogate-n200":
         return run_surrogate(args)
+    if args.workload == "latency-n1000":
+        return run_latency(args)
     if args.workload == "oos-n200":
         return run_oos(args)
     return run_ours(args)
