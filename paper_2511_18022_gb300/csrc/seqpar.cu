@@ -80,30 +80,58 @@ __global__ void seqpar_windows_kernel(SeqParParams a)
 }
 
 // Transfer matrix of block b of scenario s: kSeqW threads, thread j owns
-// column j (the image of unit state j); rows live in a circular buffer.
+// column j (the image of unit state j). The state is kept per position p in
+// a ring (slot p mod kSeqW; windows are at most kSeqW long), and the window
+// minimum by the two-stack method: the older part of the window [lo, m) has
+// suffix minima SF, the newer part [m, i-1] a running minimum bm. When the
+// window start passes m, the suffix minima are rebuilt over the whole window
+// and m moves to i. Every column walks the same window starts (they depend
+// on the scenario only), so the rebuilds happen at the same positions in all
+// threads: O(1) amortised work per position, with no divergence.
 __global__ void __launch_bounds__(kSeqW) seqpar_block_kernel(SeqParParams a)
 {
-    __shared__ int Mx[kSeqW][kSeqW + 1];          // [row slot][column]
+    __shared__ int G[kSeqW][kSeqW + 1];           // [slot of position][column]
+    __shared__ int SF[kSeqW][kSeqW + 1];          // suffix minima of the older part
+    __shared__ int s_lo[kSeqBlock], s_c[kSeqBlock];
     const int s = blockIdx.y, b = blockIdx.x, j = threadIdx.x, n = a.n;
     if (s >= a.S || a.flags[s]) return;
     const int i0 = b * kSeqBlock + 1, i1 = min(n, i0 + kSeqBlock - 1);
-    for (int r = 0; r < kSeqW; ++r) Mx[r][j] = r == j ? 0 : kInf;    // identity
-    int head = 0;                                  // slot of state row 0
-    for (int i = i0; i <= i1; ++i) {
-        const int len = i - a.lo[(long long)s * n + (i - 1)];      // window rows 0..len-1
-        int m = kInf;
-        for (int r = 0; r < len; ++r) m = min(m, Mx[(head + r) & (kSeqW - 1)][j]);
-        const int row0 = sat_add(m, a.tab[i - 1].c);
-        head = (head - 1) & (kSeqW - 1);           // shift: old rows move down by one
-        Mx[head][j] = row0;
+    for (int u = j; u < kSeqBlock; u += kSeqW) {
+        const int i = i0 + u;
+        s_lo[u] = i <= i1 ? a.lo[(long long)s * n + (i - 1)] : 0;
+        s_c[u] = i <= i1 ? a.tab[i - 1].c : 0;
     }
-    // Stored transposed, out[c * kSeqW + r] = M[r][c], so that the fold reads
-    // it with unit stride; thread j writes element j of every stored row
-    // (coalesced), reading row j of M from the other threads' columns.
+    // the unit state: position i0 - 1 - j holds 0, the other kSeqW - 1 earlier
+    // positions +inf; all of them form the older part (m = i0)
+    for (int r = 0; r < kSeqW; ++r) {
+        const int p = i0 - 1 - r;
+        G[p & (kSeqW - 1)][j] = r == j ? 0 : kInf;
+        SF[p & (kSeqW - 1)][j] = r >= j ? 0 : kInf;      // min over [p, i0 - 1]
+    }
+    __syncthreads();
+    int m = i0, bm = kInf;
+    for (int i = i0; i <= i1; ++i) {
+        const int lo = s_lo[i - i0];
+        if (lo >= m) {                                   // uniform across the block
+            int run = kInf;
+            for (int p = i - 1; p >= lo; --p) {
+                run = min(run, G[p & (kSeqW - 1)][j]);
+                SF[p & (kSeqW - 1)][j] = run;
+            }
+            m = i;
+            bm = kInf;
+        }
+        const int g = sat_add(min(SF[lo & (kSeqW - 1)][j], bm), s_c[i - i0]);
+        G[i & (kSeqW - 1)][j] = g;
+        bm = min(bm, g);
+    }
+    // Row r of the block's matrix is position i1 - r. Stored transposed,
+    // out[c * kSeqW + r] = M[r][c], so that the fold reads it with unit
+    // stride; thread j writes element j of every stored row (coalesced).
     __syncthreads();
     int *out = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
-    const int slot = (head + j) & (kSeqW - 1);
-    for (int c = 0; c < kSeqW; ++c) out[c * kSeqW + j] = Mx[slot][c];
+    const int slot = (i1 - j) & (kSeqW - 1);
+    for (int c = 0; c < kSeqW; ++c) out[c * kSeqW + j] = G[slot][c];
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
