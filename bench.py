@@ -44,9 +44,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_deque_million-n1000.traffic
 
 
 def kernel_hash() -> str:
+    """Hash of the deque kernel's sources with // comments and blank lines
+    removed: a comment edit does not invalidate the recorded counters."""
     h = hashlib.sha256()
     for f in KERNEL_FILES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        for line in open(os.path.join(ROOT, f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -1,7 +1,7 @@
 // Sequence-parallel Split for few scenarios: the recursion over tour
-// positions as a product of min-plus matrices (the abstract's "min-plus
-// matrix-vector products over layered DAGs", parallel along the positions
-// rather than across scenarios).
+// positions written as a chain of min-plus matrix products over the graph of
+// positions (the abstract frames the Split that way), evaluated in parallel
+// along the positions rather than across scenarios.
 //
 // With g(p) = f(p) + c(0, sigma_{p+1}) - D[p+1] the recursion is
 // g(i) = C_i + min_{p in W(i)} g(p). The state after position i is the vector

@@ -1,6 +1,6 @@
 // Scenario-parallel Split: one thread evaluates SPT scenarios of one giant
-// tour, walking the tour positions i = 1..n in order (Section 3, "scenario-
-// level parallelism").
+// tour, walking the tour positions i = 1..n in order (the first of the two
+// levels of parallelism of Section 3: independent scenarios).
 //
 // The segment cost of Eq. 1 separates into a part of the first position and a
 // part of the last (both scenario-independent), so with

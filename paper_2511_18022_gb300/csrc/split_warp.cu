@@ -1,5 +1,5 @@
-// Transition-parallel Split: one warp evaluates one scenario (Section 3,
-// "transition-level parallelism"). For each position i the 32 lanes take the
+// Transition-parallel Split: one warp evaluates one scenario (the second
+// level of parallelism of Section 3: the candidate predecessors of a position). For each position i the 32 lanes take the
 // candidates p of the feasible window [mask(i), i-1] of Eq. 2/3 in a strided
 // pattern and a warp min-reduction picks the best, so the cost per position
 // is O(|window| / 32 + log 32) and no candidate bound is needed. It serves the
