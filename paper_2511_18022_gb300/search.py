@@ -1,4 +1,4 @@
-"""Local search over giant tours with the exact GPU Split as the judge and an
+"""Local search over giant tours with the exact GPU Split as the arbiter and an
 optional learned surrogate that screens neighbours.
 
 Each iteration draws random 2-opt / relocate moves of the current tour
