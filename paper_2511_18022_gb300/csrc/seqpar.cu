@@ -202,12 +202,12 @@ cudaError_t launch_seqpar(const SeqParParams &a, int esize, cudaStream_t st)
         cudaError_t e = cudaFuncSetAttribute(seqpar_windows_kernel<int16_t>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        seqpar_windows_kernel<int16_t><<<(unsigned)a.S, 256, smem, st>>>(a);
+        seqpar_windows_kernel<int16_t><<<(unsigned)a.S, 1024, smem, st>>>(a);
     } else {
         cudaError_t e = cudaFuncSetAttribute(seqpar_windows_kernel<int32_t>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        seqpar_windows_kernel<int32_t><<<(unsigned)a.S, 256, smem, st>>>(a);
+        seqpar_windows_kernel<int32_t><<<(unsigned)a.S, 1024, smem, st>>>(a);
     }
     seqpar_block_kernel<<<dim3((unsigned)a.blocks, (unsigned)a.S), kSeqW, 0, st>>>(a);
     seqpar_fold_kernel<<<(unsigned)a.S, kSeqW, 0, st>>>(a);
