@@ -148,27 +148,37 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Fold the block matrices over x_0 and write f(n); one warp pair per
-// scenario. Each (transposed) matrix is copied into shared memory with async
-// copies one block ahead of its use, so the mat-vec reads shared memory only.
-__global__ void __launch_bounds__(kSeqW) seqpar_fold_kernel(SeqParParams a)
+// Fold the block matrices over x_0 and write f(n). Each (transposed) matrix
+// is copied into shared memory with async copies one block ahead of its use.
+// 256 threads per scenario: thread (r, q) takes row r of the mat-vec over the
+// columns c = q mod 4, and two shuffles combine the four partial minima.
+// Shared rows are kFoldPitch ints apart (16-byte aligned for the copies), so
+// the 32 lanes of a warp, rows r..r+7 times q = 0..3, hit 32 distinct banks.
+constexpr int kFoldThreads = 4 * kSeqW;
+constexpr int kFoldPitch = kSeqW + 8;
+
+__global__ void __launch_bounds__(kFoldThreads) seqpar_fold_kernel(SeqParParams a)
 {
     __shared__ int x[kSeqW];
-    __shared__ __align__(16) int Mt[2][kSeqW * kSeqW];
-    const int s = blockIdx.x, r = threadIdx.x;
+    __shared__ __align__(16) int Mt[2][kSeqW * kFoldPitch];
+    const int s = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31, q = lane >> 3, r = (t >> 5) * 8 + (lane & 7);
     if (s >= a.S) return;
     if (a.flags[s]) {                              // handed to the warp kernel
-        if (r == 0) {
+        if (t == 0) {
             const unsigned long long idx = atomicAdd(a.acc + ACC_OVERFLOW, 1ull);
             a.list[idx] = s;
         }
         return;
     }
-    x[r] = r == 0 ? a.g0 : kInf;
-    auto load = [&](int b) {   // 16-byte chunks of matrix b, linear and coalesced
+    if (t < kSeqW) x[t] = t == 0 ? a.g0 : kInf;
+    auto load = [&](int b) {   // 16-byte chunks of matrix b: coalesced reads, padded rows
         const int *M = a.mats + ((long long)s * a.blocks + b) * kSeqW * kSeqW;
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&Mt[b & 1][0]);
-        for (int k = r; k < kSeqW * kSeqW / 4; k += kSeqW) cp_async16(dst + 16u * k, M + 4 * k);
+        for (int k = t; k < kSeqW * kSeqW / 4; k += kFoldThreads) {
+            const int c = k / (kSeqW / 4), part = k % (kSeqW / 4);
+            cp_async16(dst + 4u * (c * kFoldPitch + 4 * part), M + 4 * k);
+        }
         cp_async_commit();
     };
     load(0);
@@ -182,13 +192,18 @@ __global__ void __launch_bounds__(kSeqW) seqpar_fold_kernel(SeqParParams a)
         __syncthreads();           // every thread's part of matrix b, and x
         const int *M = Mt[b & 1];
         int v = kInf;
-#pragma unroll 16
-        for (int c = 0; c < kSeqW; ++c) v = min(v, sat_add(M[c * kSeqW + r], x[c]));
+#pragma unroll
+        for (int k = 0; k < kSeqW / 4; ++k) {
+            const int c = 4 * k + q;
+            v = min(v, sat_add(M[c * kFoldPitch + r], x[c]));
+        }
+        v = min(v, __shfl_xor_sync(0xffffffffu, v, 8));
+        v = min(v, __shfl_xor_sync(0xffffffffu, v, 16));
         __syncthreads();           // all reads of x and of this buffer are done
-        x[r] = v;
+        if (q == 0) x[r] = v;
     }
     __syncthreads();
-    if (r == 0) {
+    if (t == 0) {
         const int cost = x[0];
         if (a.out_cost) a.out_cost[s] = cost;
         atomicAdd(a.acc + ACC_SUM, (unsigned long long)cost);
@@ -210,7 +225,7 @@ cudaError_t launch_seqpar(const SeqParParams &a, int esize, cudaStream_t st)
         seqpar_windows_kernel<int32_t><<<(unsigned)a.S, 1024, smem, st>>>(a);
     }
     seqpar_block_kernel<<<dim3((unsigned)a.blocks, (unsigned)a.S), kSeqW, 0, st>>>(a);
-    seqpar_fold_kernel<<<(unsigned)a.S, kSeqW, 0, st>>>(a);
+    seqpar_fold_kernel<<<(unsigned)a.S, kFoldThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
