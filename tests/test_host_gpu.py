@@ -134,3 +134,29 @@ def test_host_rejects_short_buffer(sp, cv):
                                     torch.cuda.current_stream().cuda_stream)
     assert rc == _lib.ERR_ARG
     assert b"allocation ends" in lib.cvrpsd_last_error(sp.ctx)
+
+
+def test_host_million_n1000_sampled(sp, cv):
+    """The bench's end-to-end call at full size: 2^20 scenarios in page-locked
+    host memory (device-generated, then four column blocks replaced by
+    host-generated ones), split in place; those blocks match the oracle and
+    the sum matches the device entry point on the same matrix."""
+    from synth import demand_columns
+    w = workload("million-n1000")
+    inst, S = w.instances[0], w.S
+    D = torch.empty((inst.n, S), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    blk, starts, host = 2048, [0, 300_001, 654_321, S - 2048], {}
+    for a in starts:
+        host[a] = demand_columns(inst.mu, inst.region, w.kind, w.scen_seeds[0] + 2, np.arange(a, a + blk), np.int16)
+        D[:, a:a + blk] = torch.from_numpy(host[a]).cuda()
+    H = torch.empty((inst.n, S), dtype=torch.int16).pin_memory()
+    H.copy_(D)
+    Hout = torch.empty(S, dtype=torch.int32).pin_memory()
+    rh = sp.split_host(inst.tour, inst.dist, H, inst.Q, inst.L, out_cost=Hout)
+    rd = sp.split(inst.tour, inst.dist, D, inst.Q, inst.L)
+    assert (rh.sum, rh.infeasible) == (rd.sum, rd.infeasible)
+    got = Hout.numpy()
+    for a in starts:
+        want, _, _, _ = oracle.split_costs(inst.tour, inst.dist, host[a], inst.Q, inst.L, nthreads=8)
+        assert np.array_equal(got[a:a + blk], want)

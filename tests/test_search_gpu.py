@@ -59,6 +59,24 @@ def test_split_eval_tours_matches_oracle(sp, cv):
         assert float(mean[t]) == ws / (3001 - wi)
 
 
+def test_split_eval_tours_surrogate_size(sp, cv):
+    """The search's exact evaluation at its own size: 8 tours of the
+    surrogate-n200 instance under all 65,536 scenarios, exactly as the
+    oracle sums them."""
+    w = workload("surrogate-n200")
+    inst, S = w.instances[0], w.S
+    D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], S, dtype=np.int16)
+    rng = np.random.default_rng(3)
+    tours = np.stack([inst.tour] + [rng.permutation(np.arange(1, inst.n + 1)) for _ in range(7)]).astype(np.int32)
+    sums = torch.empty(8, dtype=torch.int64, device="cuda")
+    inf = torch.empty(8, dtype=torch.int64, device="cuda")
+    cv.cvrpsd_split_eval_tours(sp.ctx, torch.from_numpy(tours).cuda(), inst.dist, torch.from_numpy(D).cuda(),
+                               inst.Q, inst.L, sums=sums, infeasible=inf)
+    for t in range(8):
+        _, ws, wi, _ = oracle.split_costs(tours[t], inst.dist, D, inst.Q, inst.L, nthreads=8)
+        assert (int(sums[t]), int(inf[t])) == (ws, wi)
+
+
 def test_neighbors_and_gather(sp, cv):
     rng = np.random.default_rng(2)
     n = 37
