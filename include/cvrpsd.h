@@ -24,8 +24,8 @@
  *    contiguous. Element type int16 (CVRPSD_I16) or int32 (CVRPSD_I32),
  *    values >= 0. `ld` >= S is the row pitch in elements.
  *  - Q >= 0 is the vehicle capacity. L is the largest number of customers on
- *    one route (the "maximum route length" Section 3 allows); L >= n means no
- *    limit. The fleet is unlimited.
+ *    one route (this library's reading of the optional route-length limit of
+ *    Section 3); L >= n means no limit. The fleet is unlimited.
  *  - A scenario in which some customer's demand exceeds Q has no feasible
  *    split (Eq. 2's window is empty): its cost is INT32_MAX, it is left out
  *    of the sum and the mean, and it is counted as infeasible; the call then
