@@ -3,6 +3,7 @@ sm_103a. Translation units compile in parallel; nothing is installed."""
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import platform
 import shutil
@@ -68,6 +69,19 @@ def build(force: bool = False, jobs: int | None = None, build_dir: str | None = 
         return lib
     bdir = build_dir or BUILD
     os.makedirs(bdir, exist_ok=True)
+    # One build at a time per directory (several ranks may start at once);
+    # whoever waited finds the library current and returns.
+    with open(os.path.join(bdir, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+                return lib
+            return _build_locked(lib, bdir, jobs, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(lib, bdir, jobs, extra_flags) -> str:
     jobs = jobs or min(len(UNITS), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda u: _compile(u, bdir, extra_flags), UNITS))
