@@ -72,10 +72,16 @@ class SearchLog:
 
 
 class LocalSearch:
-    """Best-improvement local search from `start` (host int array of ids)."""
+    """Best-improvement local search from `start` (host int array of ids).
+
+    An iteration never waits for the device: the moves of the next
+    `moves_block` iterations are drawn on the host and copied at once, the
+    best evaluated neighbour is chosen and accepted by device-side tensor
+    operations, and the per-iteration costs are read back when run() ends."""
 
     def __init__(self, ctx, inst, D, start, *, surrogate: Surrogate | None = None, M: int = 4096, k: int = 64,
-                 seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4):
+                 seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4,
+                 moves_block: int = 64):
         import torch
         self.ctx, self.inst, self.D = ctx, inst, D
         self.n = inst.n
@@ -85,8 +91,12 @@ class LocalSearch:
         self.eval = Evaluator(ctx, inst, D)
         dev = D.device
         self.cur = torch.tensor(np.asarray(start, dtype=np.int32), device=dev)
-        self.cur_cost = float(self.eval(self.cur.view(1, -1))[0].item())
-        self.moves = torch.empty((self.M, 3), dtype=torch.int32, device=dev)
+        self.cur_cost_t = self.eval(self.cur.view(1, -1))[:1].clone()     # device [1]
+        self.moves_block = moves_block
+        self._moves_host = torch.empty((moves_block, self.M, 3), dtype=torch.int32).pin_memory()
+        self._moves = torch.empty((moves_block, self.M, 3), dtype=torch.int32, device=dev)
+        self._moves_copied = torch.cuda.Event()
+        self._mi = moves_block
         self.cand = torch.empty((self.M, self.n), dtype=torch.int32, device=dev)
         self.top = torch.empty((k, self.n), dtype=torch.int32, device=dev)
         self.idx = torch.empty(k, dtype=torch.int32, device=dev)
@@ -95,12 +105,30 @@ class LocalSearch:
         self.scale = scale
         self.lr = lr
         self.new_tours, self.new_costs = [], []
+        self._trace = []
         self.log = SearchLog()
+
+    @property
+    def cur_cost(self) -> float:
+        return float(self.cur_cost_t[0].item())
+
+    def _next_moves(self):
+        import torch
+        if self._mi == self.moves_block:
+            # the previous block's copy must have left the pinned buffer
+            self._moves_copied.synchronize()
+            blk = np.stack([random_moves(self.rng, self.M, self.n) for _ in range(self.moves_block)])
+            self._moves_host.copy_(torch.from_numpy(blk))
+            self._moves.copy_(self._moves_host, non_blocking=True)
+            self._moves_copied.record()
+            self._mi = 0
+        m = self._moves[self._mi]
+        self._mi += 1
+        return m
 
     def step(self):
         import torch
-        self.moves.copy_(torch.from_numpy(random_moves(self.rng, self.M, self.n)))
-        cvrpsd_neighbors(self.ctx, self.cur, self.moves, self.cand)
+        cvrpsd_neighbors(self.ctx, self.cur, self._next_moves(), self.cand)
         if self.sur is not None:
             self.sur.predict(self.cand, self.scores)
             cvrpsd_topk(self.ctx, self.scores, self.k, self.idx)
@@ -109,14 +137,14 @@ class LocalSearch:
         else:
             chosen = self.cand[: self.k]
         costs = self.eval(chosen)
-        b = int(torch.argmin(costs).item())
-        c = float(costs[b].item())
-        if c < self.cur_cost:
-            self.cur.copy_(chosen[b])
-            self.cur_cost = c
+        b = torch.argmin(costs).view(1)
+        c = costs.index_select(0, b)
+        better = c < self.cur_cost_t
+        self.cur.copy_(torch.where(better, chosen.index_select(0, b)[0], self.cur))
+        self.cur_cost_t = torch.minimum(self.cur_cost_t, c)
+        self._trace.append(self.cur_cost_t)
         self.log.screened += self.M
         self.log.evaluated += self.k
-        self.log.costs.append(self.cur_cost)
         if self.sur is not None and self.retrain_every:
             self.new_tours.append(chosen.clone())
             self.new_costs.append(costs.to(torch.float32).clone())
@@ -135,6 +163,9 @@ class LocalSearch:
             self.step()
         torch.cuda.synchronize()
         self.log.seconds += time.perf_counter() - t0
+        if self._trace:
+            self.log.costs.extend(torch.cat(self._trace).tolist())
+            self._trace = []
         return self.log
 
 
