@@ -92,9 +92,11 @@ def split_costs(tour, dist, demand, Q: int, L: int | None = None,
     return out, int(out3[0]), int(out3[1]), int(out3[2])
 
 
-def split_routes(tour, dist, demand_col, Q: int, L: int | None = None):
+def split_routes(tour, dist, demand_col, Q: int, L: int | None = None, lib=None):
     """Optimal split of one scenario: (cost or None, list of routes as lists of
-    customer ids, predecessor array of length n+1)."""
+    customer ids, predecessor array of length n+1: pred[i] is the smallest p
+    attaining f(i), -1 where no feasible split of the first i customers
+    exists)."""
     tour = np.ascontiguousarray(tour, dtype=np.int32)
     dist = np.ascontiguousarray(dist, dtype=np.int32)
     col = np.ascontiguousarray(np.asarray(demand_col).reshape(-1), dtype=np.int32)
@@ -103,7 +105,7 @@ def split_routes(tour, dist, demand_col, Q: int, L: int | None = None):
     pred = np.full(n + 1, -1, dtype=np.int32)
     ends = np.zeros(max(n, 1), dtype=np.int32)
     cost = np.zeros(1, dtype=np.int64)
-    k = _load().oracle_split_routes(n, _ptr(tour), _ptr(dist), _ptr(col), 4, 1, 0,
+    k = (lib or _load()).oracle_split_routes(n, _ptr(tour), _ptr(dist), _ptr(col), 4, 1, 0,
                                     int(Q), L, _ptr(pred), _ptr(ends), _ptr(cost))
     if k == -2:
         raise MemoryError("oracle_split_routes")

@@ -184,6 +184,136 @@ def test_brute_force_n14(oracle_lib):
             assert as_opt(c[s]) == brute_force(tour, dist, D[:, s], Q, L)
 
 
+# ------------------------------------------------------- route recovery
+
+def route_cost(tour, dist, a, b):
+    """Cost of the route serving tour positions a+1..b (customers tour[a:b])."""
+    r = [int(c) for c in tour[a:b]]
+    inner = sum(int(dist[r[j]][r[j + 1]]) for j in range(len(r) - 1))
+    return int(dist[0][r[0]]) + inner + int(dist[r[-1]][0])
+
+
+def route_ok(tour, q_by_id, Q, L, a, b):
+    return b - a <= L and sum(int(q_by_id[int(c) - 1]) for c in tour[a:b]) <= Q
+
+
+def brute_prefix_pred(tour, dist, q_by_id, Q, L):
+    """Predecessors by enumeration, owing nothing to the oracle: F[i] is the
+    cheapest feasible cut of the first i customers, found over all 2^(i-1)
+    cut sets of that prefix; pred[i] is the smallest p whose route p+1..i is
+    feasible and closes a cheapest cut, F[p] + cost(p+1..i) = F[i] (-1 when
+    the prefix has no feasible cut)."""
+    n = len(tour)
+    F = [0] + [None] * n
+    for i in range(1, n + 1):
+        for mask in range(1 << (i - 1)):
+            cost, start, ok = 0, 0, True
+            for k in range(i):
+                if k == i - 1 or (mask >> k) & 1:
+                    if not route_ok(tour, q_by_id, Q, L, start, k + 1):
+                        ok = False
+                        break
+                    cost += route_cost(tour, dist, start, k + 1)
+                    start = k + 1
+            if ok and (F[i] is None or cost < F[i]):
+                F[i] = cost
+    pred = [-1] * (n + 1)
+    for i in range(1, n + 1):
+        if F[i] is None:
+            continue
+        for p in range(i):
+            if (F[p] is not None and route_ok(tour, q_by_id, Q, L, p, i)
+                    and F[p] + route_cost(tour, dist, p, i) == F[i]):
+                pred[i] = p
+                break
+    return F, pred
+
+
+def routes_from_pred(tour, pred):
+    """Walk the predecessors back from position n: the routes in tour order."""
+    ends, i = [], len(tour)
+    while i > 0:
+        ends.append(i)
+        i = pred[i]
+    routes, start = [], 0
+    for e in reversed(ends):
+        routes.append([int(c) for c in tour[start:e]])
+        start = e
+    return routes
+
+
+def tie_cases():
+    """Instances with many equal-cost cuts, where the tie rule decides."""
+    out = []
+    for n in (4, 6, 8):
+        # free travel between customers, unit depot legs: every cut with the
+        # same number of routes costs the same
+        dist = np.zeros((n + 1, n + 1), dtype=np.int32)
+        dist[0, 1:] = 1
+        dist[1:, 0] = 1
+        tour = np.arange(1, n + 1, dtype=np.int32)
+        out.append((tour, dist, np.ones((n, 3), np.int32) * [[1, 2, 3]], 4, n))
+        # collinear, symmetric about the depot: customers at -k and +k on a line
+        pts = [[0, 0]] + [[(k // 2 + 1) * (1 if k % 2 else -1), 0] for k in range(n)]
+        pts = np.array(pts)
+        dist = np.abs(pts[:, None, 0] - pts[None, :, 0]).astype(np.int32)
+        out.append((np.arange(1, n + 1, dtype=np.int32)[::-1].copy(), dist,
+                    np.array([[2, 1, 3]] * n, np.int32), 5, 3))
+        # duplicate coordinates: pairs of customers at the same point
+        pts = np.array([[50, 50]] + [[10 * (k // 2), 7 * (k // 2)] for k in range(n)])
+        dist = np.floor(np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1)) + 0.5).astype(np.int32)
+        out.append((np.arange(1, n + 1, dtype=np.int32), dist,
+                    np.array([[1, 0, 2]] * n, np.int32), 3, n))
+    return out
+
+
+def route_pin_cases():
+    return brute_cases() + tie_cases()
+
+
+def check_routes(tour, dist, D, Q, L, lib=None):
+    """Oracle predecessors and routes against enumeration; returns the first
+    mismatch as a string, or None."""
+    for s in range(D.shape[1]):
+        q = D[:, s]
+        F, want_pred = brute_prefix_pred(tour, dist, q, Q, L)
+        cost, routes, pred = oracle.split_routes(tour, dist, q, Q, L, lib=lib)
+        if list(pred[1:]) != want_pred[1:]:
+            return f"pred {list(pred[1:])} != {want_pred[1:]}"
+        n = len(tour)
+        if F[n] is None:
+            if cost is not None:
+                return "infeasible scenario given a cost"
+            continue
+        if cost != F[n] or routes != routes_from_pred(tour, want_pred):
+            return f"routes {routes} (cost {cost}) != {routes_from_pred(tour, want_pred)} ({F[n]})"
+    return None
+
+
+def test_route_recovery_matches_enumeration(oracle_lib):
+    """Whole predecessor array (smallest optimal p, Section 3 reading 7) and
+    the routes walked back from it, on the random brute-force cases and on
+    tie-heavy instances."""
+    for tour, dist, D, Q, L in route_pin_cases():
+        assert check_routes(tour, dist, D, Q, L) is None
+
+
+def test_tie_cases_have_ties(oracle_lib):
+    """The tie-heavy instances really have several optimal predecessors at
+    some position (else they would not test the tie rule)."""
+    seen = 0
+    for tour, dist, D, Q, L in tie_cases():
+        q = D[:, 0]
+        F, pred = brute_prefix_pred(tour, dist, q, Q, L)
+        for i in range(1, len(tour) + 1):
+            if F[i] is None:
+                continue
+            opt = [p for p in range(i) if F[p] is not None and route_ok(tour, q, Q, L, p, i)
+                   and F[p] + route_cost(tour, dist, p, i) == F[i]]
+            seen += len(opt) > 1
+    assert seen >= 10
+
+
 # ------------------------------------------------------- second algorithm
 
 @pytest.mark.parametrize("name,S", [("plain-n50", 1000), ("corr-n200", 1500)])
@@ -292,6 +422,16 @@ MUTANTS = {
     "missing predecessor cost": ("int64_t cost = f[p] +", "int64_t cost = 0 +"),
 }
 
+# Slips in route recovery; caught by the predecessor / route pins. (Each
+# keeps every predecessor below its position, so the walk-back ends.)
+ROUTE_MUTANTS = {
+    "largest p on ties": ("if (cost < best || (cost == best && p < best_p))", "if (cost < best)"),
+    "predecessor shifted": ("best_p = p;", "best_p = p > 0 ? p - 1 : p;"),
+    "route end off by one": ("route_end[k++] = stack_i;", "route_end[k++] = stack_i - 1;"),
+    "walk-back skips a route": ("stack_i = pred[stack_i];",
+                                "stack_i = pred[stack_i] > 0 ? pred[pred[stack_i]] : 0;"),
+}
+
 
 @pytest.mark.parametrize("label", list(MUTANTS))
 def test_pins_catch_mutants(oracle_lib, tmp_path, label):
@@ -314,3 +454,21 @@ def test_pins_catch_mutants(oracle_lib, tmp_path, label):
         if caught:
             break
     assert caught, f"no pin caught the mutant: {label}"
+
+
+def build_mutant(tmp_path, old, new):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, old
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread",
+                           str(mpath), "-o", str(so)])
+    return oracle.bind(str(so))
+
+
+@pytest.mark.parametrize("label", list(ROUTE_MUTANTS))
+def test_route_pins_catch_mutants(oracle_lib, tmp_path, label):
+    lib = build_mutant(tmp_path, *ROUTE_MUTANTS[label])
+    assert any(check_routes(*case, lib=lib) is not None for case in route_pin_cases()), \
+        f"no route pin caught the mutant: {label}"
