@@ -123,6 +123,19 @@ int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats);
  * durations in cvrpsd_stats. Off by default. */
 int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on);
 
+/* Input errors of calls that did not wait. A Split call that requests no
+ * host output returns once its work is enqueued, before the kernels have
+ * looked at the demands; a negative demand found there leaves that
+ * scenario's out_cost at INT32_MAX (counted as infeasible in the device
+ * accumulators) and cannot be returned by the call itself. Every Split on
+ * the context also records such findings in a status word that only this
+ * function clears: it waits for `stream` (which must be ordered after the
+ * calls to check), returns CVRPSD_ERR_DEVICE_STATUS if any Split since the
+ * previous check found a negative demand (CVRPSD_OK otherwise), and clears
+ * the record. Calls that return host outputs report the error themselves as
+ * well. */
+int cvrpsd_check_inputs(cvrpsd_ctx *ctx, void *stream);
+
 /* Test hook for the error paths: after `after` more device or pinned-host
  * allocations made for `ctx` (its scratch, batches, surrogates), the next one
  * fails as if memory had run out (the call returns CVRPSD_ERR_NOMEM and
@@ -415,6 +428,14 @@ int cvrpsd_surrogate_state(cvrpsd_surrogate *sur, void *h_get, const void *h_set
  * clears the accumulators it needs, but two calls whose work overlaps on the
  * GPU (different streams, or host threads) race on it and must be serialised
  * by the caller. Errors are returned as codes only (no message).
+ *
+ * The tour table travels through one process-wide host staging buffer, so a
+ * call on a stream that is being captured into a CUDA graph is refused with
+ * CVRPSD_ERR_UNSUPPORTED (a recorded copy would read that buffer when the
+ * graph runs, after later calls have changed it). Without host outputs the
+ * call returns before its kernels run: a negative demand then shows only as
+ * that scenario's INT32_MAX cost; request a host output to have it reported
+ * as CVRPSD_ERR_DEVICE_STATUS.
  */
 int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n,
                               const int32_t *dist, const void *demand,

@@ -19,7 +19,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_autotune", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
@@ -91,6 +91,13 @@ def cvrpsd_set_profiling(ctx, on: bool) -> None:
 def cvrpsd_debug_fail_alloc(ctx, after: int) -> None:
     """Test hook: make the (after+1)-th next allocation of the context fail."""
     _lib.check(ctx, _lib.load().cvrpsd_debug_fail_alloc(ctx, int(after)))
+
+
+def cvrpsd_check_inputs(ctx, stream=None) -> None:
+    """Wait for `stream`; raise CvrpsdError(ERR_DEVICE_STATUS) if a Split on
+    the context since the last check found a negative demand (the record is
+    cleared either way)."""
+    _lib.check(ctx, _lib.load().cvrpsd_check_inputs(ctx, _stream_ptr(stream)))
 
 
 def cvrpsd_last_stats(ctx) -> dict:
@@ -568,6 +575,9 @@ class Splitter:
 
     def profiling(self, on: bool = True):
         cvrpsd_set_profiling(self.ctx, on)
+
+    def check_inputs(self, stream=None):
+        cvrpsd_check_inputs(self.ctx, stream)
 
     def split(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
         return cvrpsd_split_eval(self.ctx, tour, dist, demand, Q, L, **kw)

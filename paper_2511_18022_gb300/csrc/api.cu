@@ -107,8 +107,12 @@ int ensure_scratch(cvrpsd_ctx *ctx, long long S)
 {
     // Each resource on its own: after a failed allocation the next call
     // retries only what is still missing.
-    if (!ctx->d_acc) CK(dev_alloc(ctx, &ctx->d_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMalloc(acc)");
-    if (!ctx->h_acc) CK(host_alloc(ctx, &ctx->h_acc, ACC_WORDS * sizeof(unsigned long long)), "cudaMallocHost(acc)");
+    if (!ctx->d_acc) {
+        CK(dev_alloc(ctx, &ctx->d_acc, ACC_ALLOC_WORDS * sizeof(unsigned long long)), "cudaMalloc(acc)");
+        // the sticky status word starts clear and is never zeroed per call
+        CK(cudaMemset(ctx->d_acc, 0, ACC_ALLOC_WORDS * sizeof(unsigned long long)), "clear accumulators");
+    }
+    if (!ctx->h_acc) CK(host_alloc(ctx, &ctx->h_acc, ACC_ALLOC_WORDS * sizeof(unsigned long long)), "cudaMallocHost(acc)");
     if (!ctx->d_tab) CK(dev_alloc(ctx, &ctx->d_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMalloc(tab)");
     if (!ctx->h_tab) CK(host_alloc(ctx, &ctx->h_tab, (CVRPSD_MAX_N + 1) * sizeof(TourStep)), "cudaMallocHost(tab)");
     if (!ctx->ev_tab) CK(cudaEventCreateWithFlags(&ctx->ev_tab, cudaEventDisableTiming), "cudaEventCreate");
@@ -259,6 +263,23 @@ int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on)
         for (cudaEvent_t &e : ctx->ev_t) CK(cudaEventCreate(&e), "cudaEventCreate");
     }
     ctx->profiling = on ? 1 : 0;
+    return CVRPSD_OK;
+}
+
+int cvrpsd_check_inputs(cvrpsd_ctx *ctx, void *stream_ptr)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->d_acc || !ctx->h_acc) return CVRPSD_OK;   // no Split has run on this context
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(ctx->h_acc + ACC_STICKY, ctx->d_acc + ACC_STICKY, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, stream),
+       "read status");
+    CK(cudaMemsetAsync(ctx->d_acc + ACC_STICKY, 0, sizeof(unsigned long long), stream), "clear status");
+    CK(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    if (ctx->h_acc[ACC_STICKY] & ST_NEGATIVE_DEMAND)
+        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "negative demand found by a Split since the last check");
     return CVRPSD_OK;
 }
 

@@ -6,8 +6,12 @@
 
 namespace cvrpsd {
 
-// Accumulator words written by the Split kernels (device, zeroed per call).
-enum AccWord { ACC_SUM = 0, ACC_INFEASIBLE = 1, ACC_OVERFLOW = 2, ACC_STATUS = 3, ACC_WORDS = 4 };
+// Accumulator words written by the Split kernels (device). The first
+// ACC_WORDS are zeroed per call; ACC_STICKY collects the status bits of every
+// call until the host reads and clears it (cvrpsd_check_inputs), so that a
+// call that returned without waiting still has its input errors reported.
+enum AccWord { ACC_SUM = 0, ACC_INFEASIBLE = 1, ACC_OVERFLOW = 2, ACC_STATUS = 3, ACC_WORDS = 4, ACC_STICKY = 4,
+               ACC_ALLOC_WORDS = 8 };
 
 // Device status bits (ACC_STATUS).
 enum StatusBits { ST_NEGATIVE_DEMAND = 1 };

@@ -107,6 +107,15 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
     if (S > kMaxS) return CVRPSD_ERR_UNSUPPORTED;   // the set-aside list holds kMaxS scenarios
     if ((unsigned long long)ld * demand_dtype > 0xFFFFFFFFull) return CVRPSD_ERR_UNSUPPORTED;
     if (L > n) L = n;
+    // Each call stages its tour table through one process-wide host buffer.
+    // Recorded into a graph, that copy would read the buffer at replay time,
+    // after later calls have overwritten it, so a capturing stream is refused.
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &capturing) != cudaSuccess) {
+        cudaGetLastError();
+        return CVRPSD_ERR_CUDA;
+    }
+    if (capturing != cudaStreamCaptureStatusNone) return CVRPSD_ERR_UNSUPPORTED;
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {

@@ -112,7 +112,10 @@ __global__ void __launch_bounds__(128) split_warp_kernel(SplitParams p, const in
     if (lane == 0) {
         if (sum) atomicAdd(p.acc + ACC_SUM, (unsigned long long)sum);
         if (inf) atomicAdd(p.acc + ACC_INFEASIBLE, (unsigned long long)inf);
-        if (status) atomicOr(p.acc + ACC_STATUS, (unsigned long long)status);
+        if (status) {
+            atomicOr(p.acc + ACC_STATUS, (unsigned long long)status);
+            atomicOr(p.acc + ACC_STICKY, (unsigned long long)status);
+        }
     }
 }
 

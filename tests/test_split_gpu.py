@@ -239,6 +239,30 @@ def test_negative_demand_is_reported(sp, cv):
     assert e.value.code == -5
 
 
+def test_negative_demand_found_by_a_call_that_did_not_wait(sp, cv):
+    """Without host outputs the call returns before its kernels run; the
+    negative demand is then reported by cvrpsd_check_inputs, once."""
+    inst = make_instance(20, 1, 10, seed=1, Q=30)
+    try:                                                # start from a clear record (earlier
+        sp.check_inputs()                               # tests on this context fed it bad input)
+    except cv.CvrpsdError:
+        pass
+    D = np.ones((20, 100), np.int16)
+    clean = to_dev(D)
+    out = torch.zeros(100, dtype=torch.int32, device="cuda")
+    sp.split(inst.tour, inst.dist, clean, 30, 20, out_cost=out, host_outputs=False)
+    sp.check_inputs()                                   # nothing to report
+    D[4, 17] = -3
+    bad = to_dev(D)
+    sp.split(inst.tour, inst.dist, bad, 30, 20, out_cost=out, host_outputs=False)
+    sp.split(inst.tour, inst.dist, clean, 30, 20, host_outputs=False)   # a later clean call keeps the record
+    with pytest.raises(cv.CvrpsdError) as e:
+        sp.check_inputs()
+    assert e.value.code == -5
+    assert int(out[17]) == 2**31 - 1
+    sp.check_inputs()                                   # the record was cleared
+
+
 def test_argument_errors(sp, cv):
     inst = make_instance(20, 1, 10, seed=1, Q=30)
     D = to_dev(np.ones((20, 100), np.int16))

@@ -60,3 +60,29 @@ def test_noalloc_rejects_too_many_scenarios(cv):
         cv.cvrpsd_split_eval_noalloc(inst.tour, inst.dist, D.data_ptr(), inst.Q, inst.L,
                                      S=too_many, ld=too_many, dtype=cv.I32)
     assert e.value.code == -7
+
+
+def test_noalloc_refuses_a_capturing_stream(cv):
+    """The call stages its tour table through one host buffer shared by all
+    calls; recorded into a graph, that copy would read the buffer at replay
+    time. A call on a capturing stream must therefore be refused, not
+    recorded."""
+    inst, D = case("plain-n50", 256, [])
+    cv.cvrpsd_split_eval_noalloc(inst.tour, inst.dist, D, inst.Q, inst.L)   # device set-up first
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            cv.cvrpsd_split_eval_noalloc(inst.tour, inst.dist, D, inst.Q, inst.L, host_outputs=False, stream=s)
+        except cv.CvrpsdError as e:
+            code = e.code
+    assert code == -7
+    # the device is still usable and the entry point still exact
+    r = cv.cvrpsd_split_eval_noalloc(inst.tour, inst.dist, D, inst.Q, inst.L)
+    sp = cv.Splitter(0)
+    try:
+        assert r.sum == sp.split(inst.tour, inst.dist, D, inst.Q, inst.L).sum
+    finally:
+        sp.close()
