@@ -134,7 +134,11 @@ def dist_setup():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("gloo")   # timing barrier and max only; no data exchange
+        import torch
+        # CPU tensors (timing barrier, max over ranks, parity counts) over
+        # gloo; the per-step SAA all-reduce of CUDA tensors over NCCL
+        backend = "cpu:gloo,cuda:nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -142,6 +146,63 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def sum_over_ranks(world, xs):
+    if world == 1:
+        return list(xs)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(x) for x in xs], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [int(v) for v in t.tolist()]
+
+
+def _cpulist(text: str) -> set:
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus |= set(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def gpu_numa(local: int):
+    """(NUMA node, set of nearby CPUs) of GPU `local` from sysfs, found by
+    its PCI bus id (nvidia-smi); (None, None) where unknown."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=30).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}"
+        node = int(open(path + "/numa_node").read().strip())
+        cpus = _cpulist(open(path + "/local_cpulist").read())
+        return node, cpus
+    except Exception:
+        return None, None
+
+
+def pages_by_node(addr: int) -> dict:
+    """Pages per NUMA node of the mapping that holds host address `addr`
+    (/proc/self/numa_maps)."""
+    try:
+        for line in open("/proc/self/numa_maps"):
+            parts = line.split()
+            start = int(parts[0], 16)
+            with open("/proc/self/maps") as m:
+                for ml in m:
+                    a, b = (int(x, 16) for x in ml.split()[0].split("-"))
+                    if a == start:
+                        if a <= addr < b:
+                            return {kv.split("=")[0]: int(kv.split("=")[1]) for kv in parts[2:]
+                                    if kv.startswith("N") and "=" in kv}
+                        break
+    except Exception:
+        pass
+    return {}
 
 
 def max_over_ranks(world, x: float) -> float:
@@ -226,17 +287,35 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     import paper_2511_18022_gb300 as cv
-    from paper_2511_18022_gb300 import build
-    from synth import workload
+    from paper_2511_18022_gb300 import build, shard
+    from synth import demand_matrix_parallel, workload
 
     build.build()
     w = workload(args.workload, S=args.S or None)
     inst = w.instances[0]
     n, S = inst.n, w.S
+    cores = host_cores()
+    # Weak scaling over one scenario set of world * S columns: rank r splits
+    # its contiguous shard, generated on the host from the workload's seed.
+    S_total = world * S
+    lo, hi = shard.scenario_range(S_total, rank, world)
+    assert hi - lo == S
+    # The page-locked matrix is allocated by a thread running on the CPUs
+    # next to this GPU, so that its pages sit on the GPU's NUMA node (the
+    # e2e step streams it across the host link).
+    gnode, gcpus = gpu_numa(local)
+    keep = os.sched_getaffinity(0)
+    if gcpus:
+        os.sched_setaffinity(0, gcpus & set(range(os.cpu_count() or 1)) or keep)
+    H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
+    H.numpy().fill(0)
+    os.sched_setaffinity(0, keep)
+    t0 = time.perf_counter()
+    demand_matrix_parallel(inst.mu, inst.region, w.kind, w.scen_seeds[0], S, s0=lo, dtype=np.int16,
+                           workers=max(1, cores // world), out=H.numpy())
+    gen_s = time.perf_counter() - t0
+    D = H.cuda()
     sp = cv.Splitter(local)
-    D = torch.empty((n, S), dtype=torch.int16, device="cuda")
-    # each rank splits its own scenario shard (its own seed)
-    sp.gen_demand(w.scen_seeds[0] + rank, cv.GEN_CORRELATED, inst.mu, inst.region, D)
     out = torch.empty(S, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     tuned = None
@@ -246,11 +325,18 @@ def run_ours(args):
     elif not args.no_tune:
         tuned = sp.autotune(inst.tour, inst.dist, D, inst.Q, inst.L)
 
-    def step():
+    def split_shard():
         return sp.split(inst.tour, inst.dist, D, inst.Q, inst.L, out_cost=out)
 
+    def step():
+        # this rank's shard, then the exact SAA over all ranks (one int64
+        # all-reduce of the sum and the infeasible count; none on one GPU)
+        return shard.split_and_reduce(split_shard, S_total, world, device="cuda")
+
     for _ in range(args.warmup):
-        r = step()
+        g = step()
+    # integer min/max rate of this GPU (the ALU roof), measured before the timed region
+    int_ops, int_ms = cv.cvrpsd_int_rate(local)
     sp.profiling(True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -262,7 +348,7 @@ def run_ours(args):
     clocks.mark(True)
     e0.record(stream)
     for _ in range(args.steps):
-        r = step()
+        g = step()
         st = sp.stats()
         kms.append(st["kernel_ms"])
         launches += st["launches"]
@@ -276,9 +362,95 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(world, e0.elapsed_time(e1))
     ms_per_step = elapsed_ms / args.steps
     value = world * n * S * args.steps / (elapsed_ms / 1e3)
-
-    # roofline of the Split kernel
     kernel_ms = statistics.mean(kms)
+
+    # Parity of the timed run: every scenario's cost against the oracle on
+    # the same host matrix (outside the timed region).
+    parity = None
+    relax_per_cell = None
+    if not args.no_parity:
+        import oracle
+        got = out.cpu().numpy()
+        t0 = time.perf_counter()
+        want, osum, oinf, orelax = oracle.split_costs(inst.tour, inst.dist, H.numpy(), inst.Q, inst.L,
+                                                      nthreads=max(1, cores // world))
+        osec = time.perf_counter() - t0
+        local_r = split_shard()
+        mism = int((got != want).sum())
+        tot = sum_over_ranks(world, [mism, S, orelax, int(local_r.sum != osum or local_r.infeasible != oinf)])
+        relax_per_cell = tot[2] / (n * tot[1])
+        parity = {"scenarios_checked": tot[1], "mismatches": tot[0], "sum_mismatches": tot[3],
+                  "global_sum": g[0], "global_infeasible": g[1], "oracle_seconds": round(osec, 2),
+                  "oracle_threads": max(1, cores // world),
+                  "inputs": "host-generated scenario matrix (synth), the one the timed steps split"}
+
+    roofline = roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_cell, local)
+
+    # end to end from pinned host memory
+    def e2e_step():
+        # the C-ABI call on host buffers: the kernels read the page-locked
+        # scenario matrix in place across the host link and write the costs
+        # back to page-locked host memory; the call returns after the stream
+        return sp.split_host(inst.tour, inst.dist, H, inst.Q, inst.L, out_cost=Hout)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        Hout = torch.empty(S, dtype=torch.int32, pin_memory=True)
+        e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": n * S * 2 + n * 8, "d2h_bytes_per_step": S * 4 + 32,
+               "steps": args.e2e_steps,
+               "host_memory": {"gpu_numa_node": gnode, "pages_by_node": pages_by_node(H.data_ptr()),
+                               "allocated_on_gpu_local_cpus": bool(gcpus)}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        Dc = oracle_sample(w, inst, args.cpu_cols)
+        v, reps, el = time_oracle(inst, Dc, args.cpu_seconds, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_cols} host-generated scenarios of this instance, "
+                         f"split {reps} times in {el:.1f} s on {cores} threads"}
+
+    if rank == 0:
+        metric = METRIC if parity and parity["mismatches"] == 0 and parity["sum_mismatches"] == 0 else \
+            METRIC.replace(" (bit-exact)", "")
+        line = {
+            "metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": workload_config(w, inst) | {
+                "kernel": f"deque threads={st['threads']} spt={st['spt']} ring={st['ring']}",
+                "shape_source": "fixed" if args.shape else ("autotuned" if tuned else "library default"),
+                "parallelism": (f"scenario shards x{world} of one {S_total}-scenario set, one int64 "
+                                f"all-reduce (NCCL) of the SAA per step") if world > 1 else "one GPU"},
+            "roofline": roofline, "parity": parity, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "result": {"sum": g[0], "infeasible": g[1], "mean": g[2],
+                       "overflow_scenarios": overflow // max(args.steps, 1)},
+            "setup": {"host_generation_s": round(gen_s, 2)},
+        }
+        print(json.dumps(line))
+    sp.close()
+    return 0
+
+
+def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_cell, local) -> dict:
+    """Both roofs of the Split kernel. HBM: its algorithmic bytes (2 B per
+    demand read + 4 B per cost written + 8 B per position of table) over its
+    mean CUDA-event time, against the measured copy bandwidth. Integer ALU:
+    the literal Eq. 3 work, one min per feasible (p, i) candidate (the
+    oracle's exact relaxation count) plus 6 operations per cell (load prefix,
+    window start, the two cost terms, the demand unpack), against the
+    measured min/max rate. The headline fraction is the binding roof's floor
+    time over the kernel time."""
+    import torch
     algo_bytes = n * S * 2 + S * 4 + n * 8
     peak, peak_kind = peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
@@ -291,75 +463,36 @@ def run_ours(args):
             winst = t.get("inst_executed", {}).get(shape)
     except Exception:
         pass
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "split_deque_kernel", "kernel_ms": round(kernel_ms, 4),
-                "algorithmic_bytes": algo_bytes}
-    # The kernel is bound by instruction issue: warp instructions per launch
-    # (ncu, same kernel source and shape) against one instruction per clock per
-    # scheduler, 4 schedulers per SM, at the SM clock sampled in the timed region.
+    hbm = {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+           "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": algo_bytes,
+           "floor_ms": round(algo_bytes / (peak * 1e9) * 1e3, 4)}
+    roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": peak, "unit": "GB/s", "frac": hbm["frac"],
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": "split_deque_kernel",
+            "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes": algo_bytes, "hbm": hbm}
+    if relax_per_cell is not None and int_ops:
+        ops_per_cell = relax_per_cell + 6.0
+        ops = ops_per_cell * n * S
+        alu = {"achieved": round(ops / (kernel_ms / 1e3) / 1e12, 3), "peak": round(int_ops / 1e12, 3),
+               "unit": "T int32 ops/s", "frac": round(ops / (kernel_ms / 1e3) / int_ops, 4),
+               "relaxations_per_cell": round(relax_per_cell, 4), "ops_per_cell": round(ops_per_cell, 4),
+               "peak_kind": "measured (cvrpsd_int_rate: 32-bit min/max chains, full grid, "
+                            f"{int_ms:.2f} ms)", "floor_ms": round(ops / int_ops * 1e3, 4)}
+        roof["alu"] = alu
+        if alu["floor_ms"] > hbm["floor_ms"]:
+            roof.update({"bound": "alu", "achieved": alu["achieved"], "peak": alu["peak"], "unit": alu["unit"],
+                         "frac": alu["frac"], "peak_kind": alu["peak_kind"]})
+    # Instruction issue: warp instructions per launch (ncu, same kernel source
+    # and shape) against one instruction per clock per scheduler, 4 schedulers
+    # per SM, at the SM clock sampled in the timed region.
     if winst and clk.get("sm_mhz"):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         ipeak = sms * 4 * clk["sm_mhz"] * 1e6
         iach = winst / (kernel_ms / 1e3)
-        roofline["issue"] = {"achieved": round(iach / 1e9, 1), "peak": round(ipeak / 1e9, 1),
-                             "unit": "G warp-instructions/s", "frac": round(iach / ipeak, 4),
-                             "warp_instructions_per_launch": winst,
-                             "per_warp_position": round(winst / (S / 32 * n), 2)}
-
-    # end to end from pinned host memory
-    if args.e2e_steps > 0:
-        H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
-        H.copy_(D)
-        Hout = torch.empty(S, dtype=torch.int32, pin_memory=True)
-        torch.cuda.synchronize()
-
-    def e2e_step():
-        # the C-ABI call on host buffers: the kernels read the page-locked
-        # scenario matrix in place across the host link and write the costs
-        # back to page-locked host memory; the call returns after the stream
-        return sp.split_host(inst.tour, inst.dist, H, inst.Q, inst.L, out_cost=Hout)
-
-    e2e = None
-    if args.e2e_steps > 0:
-        e2e_step()
-        barrier(world)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-        e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": n * S * 2 + n * 8, "d2h_bytes_per_step": S * 4 + 32,
-               "steps": args.e2e_steps}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cores = host_cores()
-        Dc = oracle_sample(w, inst, args.cpu_cols)
-        v, reps, el = time_oracle(inst, Dc, args.cpu_seconds, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_cols} host-generated scenarios of this instance, "
-                         f"split {reps} times in {el:.1f} s on {cores} threads"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
-            "data": "synthetic", "config": workload_config(w, inst) | {
-                "kernel": f"deque threads={st['threads']} spt={st['spt']} ring={st['ring']}",
-                "shape_source": "fixed" if args.shape else ("autotuned" if tuned else "library default"),
-                "parallelism": f"scenario shards x{world}"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
-            "result": {"sum": r.sum, "infeasible": r.infeasible, "mean": r.mean,
-                       "overflow_scenarios": overflow // max(args.steps, 1)},
-        }
-        print(json.dumps(line))
-    sp.close()
-    return 0
+        roof["issue"] = {"achieved": round(iach / 1e9, 1), "peak": round(ipeak / 1e9, 1),
+                         "unit": "G warp-instructions/s", "frac": round(iach / ipeak, 4),
+                         "warp_instructions_per_launch": winst,
+                         "per_warp_position": round(winst / (S / 32 * n), 2)}
+    return roof
 
 
 def run_batched(args):
@@ -617,6 +750,7 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=8192)
     ap.add_argument("--ref-cols", type=int, default=8192)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the full oracle comparison of the timed run")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default shape)")
     ap.add_argument("--train-pairs", type=int, default=200_000, help="surrogate-n200: labelled tours")
     ap.add_argument("--epochs", type=int, default=8, help="surrogate-n200: training epochs")

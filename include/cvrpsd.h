@@ -405,6 +405,19 @@ int cvrpsd_surrogate_params(cvrpsd_surrogate *sur, float *h_get, const float *h_
  */
 int cvrpsd_surrogate_state(cvrpsd_surrogate *sur, void *h_get, const void *h_set, int64_t *bytes);
 
+/*
+ * Measured rate of 32-bit integer min/max instructions on `device` (the
+ * operation of Eq. 3's window minimum: one min per candidate predecessor),
+ * for the integer-ALU roofline of a Split launch. Runs one kernel of eight
+ * independent min/max chains per thread on a full grid (every SM at full
+ * occupancy), `iters` x 64 min/max per thread, timed with CUDA events on
+ * `stream`. *ops_per_s receives thread-level operations per second (one warp
+ * instruction = 32 operations), *ms (may be NULL) the kernel time.
+ * Synchronous; allocates 4 bytes of device memory. Not a step of the paper's
+ * method: a measurement helper.
+ */
+int cvrpsd_int_rate(int32_t device, int32_t iters, double *ops_per_s, double *ms, void *stream);
+
 /* Largest S accepted by cvrpsd_split_eval_noalloc. */
 #define CVRPSD_NOALLOC_MAX_S 1048576
 

@@ -19,7 +19,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_int_rate", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_autotune", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
@@ -98,6 +98,15 @@ def cvrpsd_check_inputs(ctx, stream=None) -> None:
     the context since the last check found a negative demand (the record is
     cleared either way)."""
     _lib.check(ctx, _lib.load().cvrpsd_check_inputs(ctx, _stream_ptr(stream)))
+
+
+def cvrpsd_int_rate(device: int = 0, iters: int = 20000, stream=None) -> tuple[float, float]:
+    """(32-bit integer min/max operations per second, kernel ms) measured on
+    `device`: the integer-ALU peak of the Split's window minimum."""
+    ops, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _lib.check(None, _lib.load().cvrpsd_int_rate(int(device), int(iters), ctypes.byref(ops), ctypes.byref(ms),
+                                                 _stream_ptr(stream)))
+    return ops.value, ms.value
 
 
 def cvrpsd_last_stats(ctx) -> dict:

@@ -35,7 +35,7 @@ EXPORTS = [
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
     "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
     "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params", "cvrpsd_surrogate_state",
-    "cvrpsd_surrogate_set_scale",
+    "cvrpsd_surrogate_set_scale", "cvrpsd_int_rate",
 ]
 SURROGATE_PARAMS = 67841
 NOALLOC_MAX_S = 1048576
@@ -96,6 +96,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_set_profiling.argtypes = [vp, i32]
     lib.cvrpsd_debug_fail_alloc.argtypes = [vp, ctypes.c_int32]
     lib.cvrpsd_check_inputs.argtypes = [vp, vp]
+    lib.cvrpsd_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_split_eval_host.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_gen_demand.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, i32, i64, i64, i32, vp, vp]

@@ -32,6 +32,7 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("mlp.cu", [], "mlp.o"),
     ("search_api.cu", [], "search_api.o"),
     ("noalloc.cu", [], "noalloc.o"),
+    ("probe.cu", [], "probe.o"),
 ]
 
 

@@ -17,14 +17,26 @@ def scenario_range(S: int, rank: int, world: int) -> tuple[int, int]:
     return S * rank // world, S * (rank + 1) // world
 
 
-def allreduce_saa(local_sum: int, local_infeasible: int, S_total: int):
+def allreduce_saa(local_sum: int, local_infeasible: int, S_total: int, device: str = "cpu"):
     """Exact global (sum, infeasible, mean) from every rank's partial sums,
-    with torch.distributed's current process group (one int64 all-reduce)."""
+    with torch.distributed's current process group: one all-reduce of two
+    int64 on `device` ("cuda" goes over NCCL, "cpu" over gloo)."""
     import torch
     import torch.distributed as dist
-    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
-    t = torch.tensor([int(local_sum), int(local_infeasible)], dtype=torch.int64, device=dev)
+    t = torch.tensor([int(local_sum), int(local_infeasible)], dtype=torch.int64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     total, inf = int(t[0].item()), int(t[1].item())
     feas = S_total - inf
     return total, inf, (total / feas if feas > 0 else float("nan"))
+
+
+def split_and_reduce(split_shard, S_total: int, world: int, device: str = "cpu"):
+    """One sharded step: `split_shard()` splits this rank's scenarios and
+    returns an object with .sum and .infeasible; the global SAA follows from
+    one all-reduce (none with a single rank). Returns (sum, infeasible, mean)
+    over all S_total scenarios."""
+    r = split_shard()
+    if world == 1:
+        feas = S_total - r.infeasible
+        return r.sum, r.infeasible, (r.sum / feas if feas > 0 else float("nan"))
+    return allreduce_saa(r.sum, r.infeasible, S_total, device)

@@ -6,10 +6,11 @@ from .instances import (Instance, make_instance, instance_from_coords,
 from .scenarios import (KIND_NORMAL, KIND_CORRELATED, demand_columns,
                         demand_matrix)
 from .configs import WORKLOADS, workload
+from .parallel import demand_matrix_parallel
 
 __all__ = [
     "SplitMix64", "derive_seed", "philox4x32_10", "Instance", "make_instance",
     "instance_from_coords", "batched_instances", "batched_tour_sizes",
     "rounded_euclidean", "KIND_NORMAL", "KIND_CORRELATED", "demand_columns",
-    "demand_matrix", "WORKLOADS", "workload",
+    "demand_matrix", "demand_matrix_parallel", "WORKLOADS", "workload",
 ]

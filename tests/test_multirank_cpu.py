@@ -1,7 +1,7 @@
 """The multi-rank path on CPU: two gloo ranks split one scenario set, each
-evaluates its columns, and one int64 all-reduce gives the exact global SAA
-sum; the benchmark's barrier and max-over-ranks timing helpers work across
-ranks. (The kernels run one process per GPU; here the CPU oracle stands in
+evaluates its columns, and the benchmark's step function (shard.split_and_reduce:
+one int64 all-reduce) gives the exact global SAA sum; the benchmark's barrier,
+max-over-ranks timing and sum-over-ranks parity helpers work across ranks. (The kernels run one process per GPU; here the CPU oracle stands in
 for each rank's kernel, since only the host logic is under test.)"""
 import os
 import socket
@@ -26,7 +26,7 @@ def worker(rank, world, port, S, out):
                       LOCAL_RANK=str(rank))
     import bench
     import oracle
-    from paper_2511_18022_gb300.shard import scenario_range, allreduce_saa
+    from paper_2511_18022_gb300.shard import scenario_range, split_and_reduce
     from synth import demand_columns, workload
     w_, r_, _ = bench.dist_setup()
     assert (w_, r_) == (world, rank)
@@ -35,11 +35,21 @@ def worker(rank, world, port, S, out):
     lo, hi = scenario_range(S, rank, world)
     D = demand_columns(inst.mu, inst.region, w.kind, w.scen_seeds[0], np.arange(lo, hi), np.int16)
     D[0, 0] = inst.Q + 1                                  # one infeasible scenario per rank
-    _, s, inf, _ = oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L)
-    total, tinf, mean = allreduce_saa(s, inf, S)
+
+    class R:                                               # what a Split call returns
+        pass
+
+    def split_shard():                                     # the oracle stands in for the kernel
+        r = R()
+        _, r.sum, r.infeasible, _ = oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L)
+        return r
+
+    # the benchmark's step: this rank's shard, then one all-reduce of the SAA
+    total, tinf, mean = split_and_reduce(split_shard, S, world, device="cpu")
     bench.barrier(world)
     mx = bench.max_over_ranks(world, float(rank) + 1.5)
-    out.put((rank, lo, hi, total, tinf, mean, mx))
+    counts = bench.sum_over_ranks(world, [rank + 1, 10 * rank])
+    out.put((rank, lo, hi, total, tinf, mean, mx, counts))
     import torch.distributed as dist
     dist.destroy_process_group()
 
@@ -61,13 +71,14 @@ def test_two_gloo_ranks_shard_scenarios_exactly():
     w = workload("corr-n200", S=S)
     inst = w.instances[0]
     D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], S, dtype=np.int16)
-    for (_, lo, _, _, _, _, _) in res:
+    for (_, lo, _, _, _, _, _, _) in res:
         D[0, lo] = inst.Q + 1
     _, s, inf, _ = oracle.split_costs(inst.tour, inst.dist, D, inst.Q, inst.L)
     assert [r[1:3] for r in res] == [(0, 150), (150, 301)]
     for r in res:
         assert (r[3], r[4]) == (s, inf) and r[5] == s / (S - inf)
         assert r[6] == 2.5                                # max over ranks of rank + 1.5
+        assert r[7] == [3, 10]                            # sums over ranks (parity counts)
 
 
 def test_scenario_range_partitions():

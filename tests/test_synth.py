@@ -20,6 +20,29 @@ def test_philox_known_answers():
         assert tuple(int(x) for x in got) == want
 
 
+def test_c_philox_words_match_numpy():
+    """The C Philox used for large grids gives the numpy version's words."""
+    from synth import _cphilox
+    if _cphilox.load() is None:
+        pytest.skip("no C compiler")
+    s = np.array([0, 1, 2**32 - 1, 77, 123456789], dtype=np.int64)
+    idx = np.array([0, 3, 999, 2**31], dtype=np.int64)
+    w0, w1 = _cphilox.words(s, idx, 2, 0xA4093822, 0x299F31D0)
+    ref = philox4x32_10(s[None, :], idx[:, None], 2, 0, 0xA4093822, 0x299F31D0)
+    assert (w0 == ref[0]).all() and (w1 == ref[1]).all()
+    # the first Random123 known answer has a zero counter and key
+    kat = _cphilox.words(np.array([0]), np.array([0]), 0, 0, 0)
+    assert (int(kat[0][0, 0]), int(kat[1][0, 0])) == (0x6627E8D5, 0xE169C58D)
+
+
+def test_parallel_matrix_equals_serial():
+    from synth import demand_matrix_parallel
+    inst = make_instance(30, 1, 30, seed=3, Q=200)
+    a = demand_matrix_parallel(inst.mu, inst.region, KIND_CORRELATED, 41, 5000, s0=17, workers=2, chunk=1024)
+    b = demand_matrix(inst.mu, inst.region, KIND_CORRELATED, 41, 5000, s0=17)
+    assert (a == b).all()
+
+
 def test_splitmix64_reference_outputs():
     # First outputs of the reference SplitMix64 generator seeded with 0.
     r = SplitMix64(0)
