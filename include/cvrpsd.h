@@ -125,9 +125,9 @@ int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on);
 
 /* Input errors of calls that did not wait. A Split call that requests no
  * host output returns once its work is enqueued, before the kernels have
- * looked at the demands; a negative demand found there leaves that
- * scenario's out_cost at INT32_MAX (counted as infeasible in the device
- * accumulators) and cannot be returned by the call itself. Every Split on
+ * looked at the demands; a negative demand found there (that scenario's
+ * cost is then evaluated with it read as zero) cannot be returned by the
+ * call itself. Every Split on
  * the context also records such findings in a status word that only this
  * function clears: it waits for `stream` (which must be ordered after the
  * calls to check), returns CVRPSD_ERR_DEVICE_STATUS if any Split since the
@@ -446,8 +446,8 @@ int cvrpsd_int_rate(int32_t device, int32_t iters, double *ops_per_s, double *ms
  * call on a stream that is being captured into a CUDA graph is refused with
  * CVRPSD_ERR_UNSUPPORTED (a recorded copy would read that buffer when the
  * graph runs, after later calls have changed it). Without host outputs the
- * call returns before its kernels run: a negative demand then shows only as
- * that scenario's INT32_MAX cost; request a host output to have it reported
+ * call returns before its kernels run, so a negative demand (read as zero by
+ * the kernels) is not reported; request a host output to have it reported
  * as CVRPSD_ERR_DEVICE_STATUS.
  */
 int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n,
