@@ -158,53 +158,6 @@ def sum_over_ranks(world, xs):
     return [int(v) for v in t.tolist()]
 
 
-def _cpulist(text: str) -> set:
-    cpus = set()
-    for part in text.strip().split(","):
-        if "-" in part:
-            a, b = part.split("-")
-            cpus |= set(range(int(a), int(b) + 1))
-        elif part:
-            cpus.add(int(part))
-    return cpus
-
-
-def gpu_numa(local: int):
-    """(NUMA node, set of nearby CPUs) of GPU `local` from sysfs, found by
-    its PCI bus id (nvidia-smi); (None, None) where unknown."""
-    try:
-        bus = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=pci.bus_id",
-                              "--format=csv,noheader"], capture_output=True, text=True,
-                             timeout=30).stdout.strip().lower()
-        dom, rest = bus.split(":", 1)
-        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}"
-        node = int(open(path + "/numa_node").read().strip())
-        cpus = _cpulist(open(path + "/local_cpulist").read())
-        return node, cpus
-    except Exception:
-        return None, None
-
-
-def pages_by_node(addr: int) -> dict:
-    """Pages per NUMA node of the mapping that holds host address `addr`
-    (/proc/self/numa_maps)."""
-    try:
-        for line in open("/proc/self/numa_maps"):
-            parts = line.split()
-            start = int(parts[0], 16)
-            with open("/proc/self/maps") as m:
-                for ml in m:
-                    a, b = (int(x, 16) for x in ml.split()[0].split("-"))
-                    if a == start:
-                        if a <= addr < b:
-                            return {kv.split("=")[0]: int(kv.split("=")[1]) for kv in parts[2:]
-                                    if kv.startswith("N") and "=" in kv}
-                        break
-    except Exception:
-        pass
-    return {}
-
-
 def max_over_ranks(world, x: float) -> float:
     if world == 1:
         return x
@@ -287,7 +240,7 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     import paper_2511_18022_gb300 as cv
-    from paper_2511_18022_gb300 import build, shard
+    from paper_2511_18022_gb300 import build, hostmem, shard
     from synth import demand_matrix_parallel, workload
 
     build.build()
@@ -303,13 +256,7 @@ def run_ours(args):
     # The page-locked matrix is allocated by a thread running on the CPUs
     # next to this GPU, so that its pages sit on the GPU's NUMA node (the
     # e2e step streams it across the host link).
-    gnode, gcpus = gpu_numa(local)
-    keep = os.sched_getaffinity(0)
-    if gcpus:
-        os.sched_setaffinity(0, gcpus & set(range(os.cpu_count() or 1)) or keep)
-    H = torch.empty((n, S), dtype=torch.int16, pin_memory=True)
-    H.numpy().fill(0)
-    os.sched_setaffinity(0, keep)
+    H, placement = hostmem.pinned_near_gpu((n, S), torch.int16, local)
     t0 = time.perf_counter()
     demand_matrix_parallel(inst.mu, inst.region, w.kind, w.scen_seeds[0], S, s0=lo, dtype=np.int16,
                            workers=max(1, cores // world), out=H.numpy())
@@ -407,8 +354,7 @@ def run_ours(args):
         e2e = {"value": world * n * S * args.e2e_steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": n * S * 2 + n * 8, "d2h_bytes_per_step": S * 4 + 32,
                "steps": args.e2e_steps,
-               "host_memory": {"gpu_numa_node": gnode, "pages_by_node": pages_by_node(H.data_ptr()),
-                               "allocated_on_gpu_local_cpus": bool(gcpus)}}
+               "host_memory": placement | {"pages_by_node": hostmem.pages_by_node(H.data_ptr())}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

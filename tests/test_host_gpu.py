@@ -160,3 +160,16 @@ def test_host_million_n1000_sampled(sp, cv):
     for a in starts:
         want, _, _, _ = oracle.split_costs(inst.tour, inst.dist, host[a], inst.Q, inst.L, nthreads=8)
         assert np.array_equal(got[a:a + blk], want)
+
+
+def test_pinned_matrix_sits_on_the_gpus_numa_node():
+    """The e2e matrix is allocated by a thread bound to the CPUs next to the
+    GPU; every resident page of it must then be on the GPU's NUMA node."""
+    from paper_2511_18022_gb300 import hostmem
+    node, cpus = hostmem.gpu_numa(0)
+    if node is None or node < 0:
+        pytest.skip("the GPU reports no NUMA node")
+    H, placement = hostmem.pinned_near_gpu((64, 1 << 16), torch.int16, 0)
+    pages = hostmem.pages_by_node(H.data_ptr())
+    assert placement["bound"] and pages, placement
+    assert set(pages) == {f"N{node}"}, pages

@@ -90,3 +90,9 @@ def test_scenario_range_partitions():
             assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
     with pytest.raises(ValueError):
         scenario_range(10, 2, 2)
+
+
+def test_cpulist_parsing():
+    from paper_2511_18022_gb300.hostmem import _cpulist
+    assert _cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert _cpulist("") == set()
