@@ -79,14 +79,28 @@ extern "C" {
 
 typedef struct cvrpsd_ctx cvrpsd_ctx;
 
+/* Walks of the deque kernel (cvrpsd_config.variant). */
+#define CVRPSD_WALK_AUTO          0   /* PARAM_TABLE where it applies, else GLOBAL_TABLE */
+#define CVRPSD_WALK_GLOBAL_TABLE  1   /* tour table in global memory; any n, spt 1 or 2 */
+#define CVRPSD_WALK_PARAM_TABLE   2   /* tour table in the launch's parameters: n <= 4064, spt 1,
+                                         int16 demands need Q < 32768; rings of 8 or 16 */
+
 /* Launch shape of the Split. threads in {64,128,256} per block, spt
  * (scenarios per thread) in {1,2}, ring (deque capacity per scenario) in
- * {16,32,64}. Zero fields mean "library default / autotuned". */
+ * {8,16,32,64} (8 only with the parameter-table walk), variant one of
+ * CVRPSD_WALK_*, rounds >= 0: with rounds = 0 every thread walks one
+ * scenario; with rounds = r >= 1 (parameter-table walk) the grid has
+ * ceil(tiles / r) blocks and each walks up to r tiles of `threads`
+ * scenarios, one after the other. Zero fields mean "library default /
+ * autotuned". A shape or walk that does not apply to a call is replaced by
+ * the nearest one that does (cvrpsd_last_stats reports what ran). */
 typedef struct {
     int32_t kernel;
     int32_t threads;
     int32_t spt;
     int32_t ring;
+    int32_t variant;
+    int32_t rounds;
 } cvrpsd_config;
 
 /* What the last Split call on a context did. */
@@ -98,6 +112,8 @@ typedef struct {
     int32_t launches;          /* kernels launched by the call */
     float kernel_ms;           /* device time of the main Split kernel, -1 unless profiling */
     float fallback_ms;         /* device time of the overflow pass, -1 unless profiling */
+    int32_t variant;           /* deque walk that ran (CVRPSD_WALK_*), 0 for other kernels */
+    int32_t rounds;            /* tiles per block of that walk (0: one scenario per thread) */
 } cvrpsd_stats;
 
 /* Create a context bound to CUDA device `device`. Allocates small scratch

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MAX_N,
-                   KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, KERNEL_SEQPAR, GEN_NORMAL, GEN_CORRELATED)
+                   KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, KERNEL_SEQPAR, GEN_NORMAL, GEN_CORRELATED,
+                   WALK_AUTO, WALK_GLOBAL_TABLE, WALK_PARAM_TABLE)
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
@@ -25,6 +26,7 @@ __all__ = [
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "KERNEL_SEQPAR", "GEN_NORMAL", "GEN_CORRELATED",
+    "WALK_AUTO", "WALK_GLOBAL_TABLE", "WALK_PARAM_TABLE",
 ]
 
 INT32_MAX = 2**31 - 1
@@ -73,8 +75,8 @@ def cvrpsd_destroy(ctx) -> None:
     _lib.check(None, _lib.load().cvrpsd_destroy(ctx))
 
 
-def cvrpsd_set_config(ctx, kernel=KERNEL_AUTO, threads=0, spt=0, ring=0) -> None:
-    cfg = Config(kernel, threads, spt, ring)
+def cvrpsd_set_config(ctx, kernel=KERNEL_AUTO, threads=0, spt=0, ring=0, variant=0, rounds=0) -> None:
+    cfg = Config(kernel, threads, spt, ring, variant, rounds)
     _lib.check(ctx, _lib.load().cvrpsd_set_config(ctx, ctypes.byref(cfg)))
 
 
@@ -313,6 +315,7 @@ def cvrpsd_autotune(ctx, tour, dist, demand, Q: int, L: int | None = None, *, S:
                                      ctypes.byref(res), _stream_ptr(stream))
     _lib.check(ctx, rc)
     return {"threads": res.best.threads, "spt": res.best.spt, "ring": res.best.ring,
+            "variant": res.best.variant, "rounds": res.best.rounds,
             "ms": res.best_ms, "dtype": res.best_dtype, "shapes_timed": res.shapes_timed}
 
 
@@ -529,6 +532,7 @@ def cvrpsd_batch_autotune(ctx, tours, S: int, stream=None) -> dict:
                                                       _stream_ptr(stream)))
     del keep
     return {"threads": res.best.threads, "spt": res.best.spt, "ring": res.best.ring,
+            "variant": res.best.variant, "rounds": res.best.rounds,
             "ms": res.best_ms, "dtype": res.best_dtype, "shapes_timed": res.shapes_timed}
 
 

@@ -24,6 +24,7 @@ I32 = 4
 MAX_N = 8191
 KERNEL_AUTO, KERNEL_DEQUE, KERNEL_WARP, KERNEL_SEQPAR = 0, 1, 2, 3
 GEN_NORMAL, GEN_CORRELATED = 0, 1
+WALK_AUTO, WALK_GLOBAL_TABLE, WALK_PARAM_TABLE = 0, 1, 2
 
 # Every symbol include/cvrpsd.h declares.
 EXPORTS = [
@@ -43,14 +44,16 @@ NOALLOC_MAX_S = 1048576
 
 class Config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("spt", ctypes.c_int32), ("ring", ctypes.c_int32)]
+                ("spt", ctypes.c_int32), ("ring", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("rounds", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("spt", ctypes.c_int32), ("ring", ctypes.c_int32),
                 ("overflow", ctypes.c_int64), ("launches", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float)]
+                ("kernel_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
+                ("variant", ctypes.c_int32), ("rounds", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):

@@ -22,6 +22,7 @@ CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-
 
 # (source, extra defines, object name)
 UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") for k in range(4)] + [
+    ("split_deque2.cu", [f"-DCVRPSD_DEQUE2_PART={k}"], f"split_deque2_{k}.o") for k in range(4)] + [
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=0"], "split_batch_0.o"),
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=1"], "split_batch_1.o"),
     ("split_warp.cu", [], "split_warp.o"),

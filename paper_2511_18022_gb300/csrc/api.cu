@@ -14,6 +14,7 @@
 
 #include "../../include/cvrpsd.h"
 #include "ctx.h"
+#include "deque2.h"
 #include "kernels.h"
 #include "tour_table.h"
 
@@ -143,7 +144,7 @@ int build_tour_table(cvrpsd_ctx *ctx, const int32_t *tour, int n, const int32_t 
 bool valid_shape(int threads, int spt, int ring)
 {
     return (threads == 64 || threads == 128 || threads == 256) && (spt == 1 || spt == 2) &&
-           (ring == 16 || ring == 32 || ring == 64);
+           (ring == 8 || ring == 16 || ring == 32 || ring == 64);
 }
 
 }  // namespace
@@ -230,6 +231,9 @@ int cvrpsd_set_config(cvrpsd_ctx *ctx, const cvrpsd_config *cfg)
     if (any_shape && !valid_shape(cfg->threads, cfg->spt, cfg->ring))
         return fail(ctx, CVRPSD_ERR_ARG, "shape threads=%d spt=%d ring=%d not supported", cfg->threads, cfg->spt,
                     cfg->ring);
+    if (cfg->variant < CVRPSD_WALK_AUTO || cfg->variant > CVRPSD_WALK_PARAM_TABLE)
+        return fail(ctx, CVRPSD_ERR_ARG, "walk variant %d unknown", cfg->variant);
+    if (cfg->rounds < 0 || cfg->rounds > 1024) return fail(ctx, CVRPSD_ERR_ARG, "rounds = %d outside 0..1024", cfg->rounds);
     ctx->cfg = *cfg;
     return CVRPSD_OK;
 }
@@ -431,6 +435,36 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
         } else {
             DequeShape shape{128, 1, 16};
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
+            // The parameter-table walk wherever it applies (one scenario per
+            // thread, no predecessor output, n <= 4064, ...).
+            const bool v2_ok = deque2_supported(p, demand_dtype);
+            const int variant = ctx->cfg.variant == CVRPSD_WALK_GLOBAL_TABLE || !v2_ok ? CVRPSD_WALK_GLOBAL_TABLE
+                              : (ctx->cfg.variant == CVRPSD_WALK_PARAM_TABLE || !ctx->cfg.threads || shape.spt == 1)
+                                  ? CVRPSD_WALK_PARAM_TABLE
+                                  : CVRPSD_WALK_GLOBAL_TABLE;
+            if (variant == CVRPSD_WALK_PARAM_TABLE) {
+                if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
+                DequeShape ran{};
+                const int rounds = ctx->cfg.rounds;
+                CK(launch_split_deque2(p, ctx->h_tab, demand_dtype, DequeShape{shape.threads, 1, shape.ring}, rounds,
+                                       &ran, stream),
+                   "split_deque2 launch");
+                if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
+                st.kernel = CVRPSD_KERNEL_DEQUE;
+                st.threads = ran.threads;
+                st.spt = 1;
+                st.ring = ran.ring;
+                st.variant = CVRPSD_WALK_PARAM_TABLE;
+                st.rounds = rounds;
+                CK(launch_split_warp(p, demand_dtype, ctx->d_list, ctx->d_acc + ACC_OVERFLOW, warp_grid,
+                                     ctx->max_smem, stream),
+                   "split_warp (set-aside scenarios) launch");
+                st.launches = 2;
+                fallback_launched = true;
+                if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
+                goto launched;
+            }
+            if (shape.ring == 8) shape.ring = 16;   // the global-table walk has rings of 16..64
             if (pred && (shape.spt != 1 || shape.threads == 64 || shape.ring == 64))
                 shape = DequeShape{128, 1, 16};      // route recovery shapes
             // Vector loads of spt demands need spt-aligned rows and base.
@@ -452,6 +486,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             st.threads = shape.threads;
             st.spt = shape.spt;
             st.ring = shape.ring;
+            st.variant = CVRPSD_WALK_GLOBAL_TABLE;
             st.launches = 1;
             // Scenarios the deque kernel set aside (ring too small, a demand above
             // Q, a negative demand) are evaluated by the warp kernel; with none
@@ -464,6 +499,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
         }
     }
+launched:
     ctx->stats = st;
     if (!out_sum && !out_infeasible && !out_mean && !host_buffers) return CVRPSD_OK;
 
@@ -569,9 +605,10 @@ bool tune_cache_lookup(const char *path, const std::string &key, cvrpsd_tune_res
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         cvrpsd_tune_result t{};
-        if (sscanf(line, "{\"key\": \"%255[^\"]\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"ms\": %f, "
-                         "\"dtype\": %d}",
-                   k, &t.best.threads, &t.best.spt, &t.best.ring, &t.best_ms, &t.best_dtype) == 6 &&
+        if (sscanf(line, "{\"key\": \"%255[^\"]\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"variant\": %d, "
+                         "\"rounds\": %d, \"ms\": %f, \"dtype\": %d}",
+                   k, &t.best.threads, &t.best.spt, &t.best.ring, &t.best.variant, &t.best.rounds, &t.best_ms,
+                   &t.best_dtype) == 8 &&
             key == k && valid_shape(t.best.threads, t.best.spt, t.best.ring)) {
             t.best.kernel = CVRPSD_KERNEL_DEQUE;
             *r = t;
@@ -599,8 +636,10 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     cvrpsd_tune_result best{};
     long long ref_sum = 0, ref_inf = 0, s_ = 0, i_ = 0;
     float ms = 0;
-    // reference: the default shape (also validates every argument)
-    rc = timed_split(ctx, cvrpsd_config{CVRPSD_KERNEL_DEQUE, 0, 0, 0}, tour, n, dist, demand, demand_dtype, S, ld,
+    // reference: the global-table walk in its default shape (also validates
+    // every argument); every candidate must reproduce its sums
+    rc = timed_split(ctx, cvrpsd_config{CVRPSD_KERNEL_DEQUE, 128, 1, 16, CVRPSD_WALK_GLOBAL_TABLE, 0}, tour, n, dist,
+                     demand, demand_dtype, S, ld,
                      Q, L, stream_ptr, &ref_sum, &ref_inf, &ms);
     if (rc < 0) {
         ctx->cfg = saved;
@@ -616,32 +655,64 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     }
     best.best_ms = 1e30f;
     int timed = 0;
-    for (int threads : {64, 128, 256})
-        for (int spt : {1, 2})
-            for (int ring : {16, 32, 64}) {
-                const cvrpsd_config cfg{CVRPSD_KERNEL_DEQUE, threads, spt, ring};
-                float t_best = 1e30f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    rc = timed_split(ctx, cfg, tour, n, dist, demand, demand_dtype, S, ld, Q, L, stream_ptr, &s_,
-                                     &i_, &ms);
-                    if (rc < 0) break;
-                    if (s_ != ref_sum || i_ != ref_inf) {
-                        ctx->cfg = saved;
-                        ctx->profiling = saved_prof;
-                        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "shape %d/%d/%d gives sum %lld, default %lld",
-                                    threads, spt, ring, s_, ref_sum);
-                    }
-                    if (rep > 0 && ms < t_best) t_best = ms;   // first run warms up
-                }
-                if (rc < 0) continue;                            // shape not launchable here
-                ++timed;
-                // the shape the library actually ran (it may shrink spt / threads to fit)
-                const cvrpsd_config ran{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring};
-                if (t_best < best.best_ms) {
-                    best.best_ms = t_best;
-                    best.best = ran;
+    // Candidates: the parameter-table walk (where it applies) over threads x
+    // ring x rounds (one scenario per thread, or the fewest whole rounds the
+    // resident grid allows and one more), then the global-table walk over
+    // threads x spt x ring.
+    std::vector<cvrpsd_config> cands;
+    SplitParams probe{};
+    probe.n = n;
+    probe.ld = ld;
+    probe.S = S;
+    probe.Q = Q;
+    probe.L = L < n ? L : n;
+    probe.K = key_scale(n);
+    if (deque2_supported(probe, demand_dtype)) {
+        for (int threads : {64, 128, 256})
+            for (int ring : {8, 16}) {
+                const int occ = deque2_blocks_per_sm(probe, demand_dtype, DequeShape{threads, 1, ring});
+                const long long tiles = (S + threads - 1) / threads;
+                const long long resident = (long long)occ * (ctx->sm_count > 0 ? ctx->sm_count : 1);
+                const int r_min = resident > 0 ? (int)std::min<long long>((tiles + resident - 1) / resident, 1024) : 0;
+                cands.push_back(cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, 0});
+                if (r_min >= 1) {
+                    cands.push_back(cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, r_min});
+                    if (r_min < 1024)
+                        cands.push_back(
+                            cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, r_min + 1});
                 }
             }
+    }
+    for (int threads : {64, 128, 256})
+        for (int spt : {1, 2})
+            for (int ring : {16, 32, 64})
+                cands.push_back(cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, spt, ring, CVRPSD_WALK_GLOBAL_TABLE, 0});
+    for (const cvrpsd_config &cfg : cands) {
+        const int threads = cfg.threads, spt = cfg.spt, ring = cfg.ring;
+        float t_best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            rc = timed_split(ctx, cfg, tour, n, dist, demand, demand_dtype, S, ld, Q, L, stream_ptr, &s_,
+                             &i_, &ms);
+            if (rc < 0) break;
+            if (s_ != ref_sum || i_ != ref_inf) {
+                ctx->cfg = saved;
+                ctx->profiling = saved_prof;
+                return fail(ctx, CVRPSD_ERR_DEVICE_STATUS,
+                            "shape %d/%d/%d walk %d rounds %d gives sum %lld, default %lld", threads, spt,
+                            ring, cfg.variant, cfg.rounds, s_, ref_sum);
+            }
+            if (rep > 0 && ms < t_best) t_best = ms;   // first run warms up
+        }
+        if (rc < 0) continue;                            // shape not launchable here
+        ++timed;
+        // the shape the library actually ran (it may shrink spt / threads to fit)
+        const cvrpsd_config ran{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring,
+                                ctx->stats.variant, ctx->stats.rounds};
+        if (t_best < best.best_ms) {
+            best.best_ms = t_best;
+            best.best = ran;
+        }
+    }
     if (!timed) {
         ctx->cfg = saved;
         ctx->profiling = saved_prof;
@@ -684,9 +755,10 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     ctx->profiling = saved_prof;
     if (cache_path) {
         if (FILE *f = fopen(cache_path, "a")) {
-            fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"ms\": %.6f, "
-                       "\"dtype\": %d}\n",
-                    key.c_str(), best.best.threads, best.best.spt, best.best.ring, best.best_ms, best.best_dtype);
+            fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"variant\": %d, "
+                       "\"rounds\": %d, \"ms\": %.6f, \"dtype\": %d}\n",
+                    key.c_str(), best.best.threads, best.best.spt, best.best.ring, best.best.variant,
+                    best.best.rounds, best.best_ms, best.best_dtype);
             fclose(f);
         }
     }

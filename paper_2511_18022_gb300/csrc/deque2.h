@@ -1,0 +1,55 @@
+// Internal interface of the second deque walk (split_deque2.cuh): its
+// parameter blocks and launcher.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+#include "tour_table.h"
+
+namespace cvrpsd {
+
+// Table capacities of the kernel-parameter tour table: 8 KB for tours up to
+// 1024 customers, and the largest that fits the 32 KB parameter space.
+constexpr int kTab2Small = 1024;
+constexpr int kTab2Large = 4064;
+
+// Table entry of position i (index i - 1): x = byte offset of sigma_i's
+// demand row (row * pitch), y = C_i. Bit m of nonpos marks prefetch block m
+// (positions 1 + m * kPrefetch ...) as holding some C_i <= 0.
+template <int CAP>
+struct TabParam {
+    uint2 e[CAP];
+    uint32_t nonpos[(CAP / kPrefetch + 31) / 32];
+};
+
+struct Walk2Params {
+    const void *demand;        // device [n][ld]
+    long long S;               // scenarios
+    long long stride;          // grid * T: scenario step between a thread's rounds
+    int32_t n, Q, L, g0;       // L > n: no route-length limit
+    uint32_t K;                // key scale: power of two > n
+    int32_t *out_cost;         // device [S] or nullptr
+    unsigned long long *acc;   // device [ACC_WORDS]
+    int32_t *ovf_list;         // device [S]
+};
+
+// Whether the second walk can run this Split (otherwise the first walk runs):
+// no predecessor output, n <= kTab2Large, demand rows addressable with
+// 32-bit byte offsets, and for int16 demands Q < 32768 (a negative demand
+// read as unsigned then exceeds Q).
+bool deque2_supported(const SplitParams &p, int esize);
+
+// Launch it. `tab` is the host copy of the tour table (TourStep rows with
+// the block flag); rounds = 0 gives one scenario per thread, rounds >= 1 a
+// grid of ceil(tiles / rounds) blocks, each walking up to `rounds` tiles of
+// T scenarios. *shape_ran receives the (threads, ring) actually launched.
+cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int esize, const DequeShape &shape,
+                                int rounds, DequeShape *shape_ran, cudaStream_t stream);
+
+// Blocks of `shape` resident per SM for this Split's kernel class (0 if the
+// class or shape is not compiled).
+int deque2_blocks_per_sm(const SplitParams &p, int esize, const DequeShape &shape);
+
+}  // namespace cvrpsd

@@ -1,0 +1,264 @@
+// Scenario-parallel Split, second walk: the same monotone-deque recursion as
+// split_deque.cuh (one thread per scenario, Section 3's scenario level;
+// Eq. 1-3 through the separable segment cost, see there), with the fixed
+// per-position work cut down:
+//
+//  - The tour table is a kernel parameter (__grid_constant__), read at a
+//    block-uniform index: one constant-bank load per position gives the
+//    demand row's byte offset (pre-multiplied by the row pitch) and C_i, so
+//    the demand address is one add and no global table load is issued.
+//  - int16 demands are read as unsigned 16-bit values. A demand above Q (a
+//    negative one reads as >= 32768 > Q) expires every deque entry, the back
+//    one included; the front walk notices when it would pass the back,
+//    marks the scenario bad and freezes it. So the per-position clamp and
+//    running maximum of the first walk are gone (int32 demands keep them).
+//  - When n * Q * K + (Q + 1) * K + n < 2^31 (checked on the host), keys
+//    never wrap and the capacity test is one signed compare (NOWRAP).
+//  - A frozen scenario (ring overflow or a bad demand) gets a front that can
+//    never expire (key and expiry at INT_MAX) and is excluded from back
+//    pops, so the per-position tests carry no freeze term.
+//  - The rings are a static shared array, so a slot's address is its masked
+//    byte offset plus a constant the loads and stores fold in.
+//  - The grid may be smaller than one thread per scenario: a thread then
+//    walks scenarios s, s + G*T, ... (every thread of a block the same
+//    number of times), which lets the host make the number of rounds an
+//    integer and avoid a part-empty last wave.
+//
+// Set-aside scenarios (ring too small, a demand above Q, a negative demand)
+// go to the warp kernel exactly as before.
+#pragma once
+
+#include <stdint.h>
+
+#include "deque2.h"
+#include "kernels.h"
+#include "split_deque.cuh"
+#include "tour_table.h"
+
+namespace cvrpsd {
+
+struct Deque2 {
+    int fg;          // front entry: g
+    int fx;          // front key K * (P(p) + Q) + p
+    int fe;          // front expiry step p + L + 1 (LCAP)
+    int bg;          // back entry: g
+    uint32_t h;      // byte offset of the front slot in the block's rings
+    uint32_t b;      // byte offset of the back slot
+    uint32_t pk;     // K * P(i)
+    uint32_t qmax;   // int32 demands only: largest demand seen (unsigned)
+    bool frozen;     // ring overflow or a bad demand: set aside, no more pops
+};
+
+// Signed capacity test of a key against K * P(i): wrapping difference, or a
+// plain compare when keys cannot wrap.
+template <bool NOWRAP>
+__device__ __forceinline__ bool key_expired(int x, uint32_t pk)
+{
+    if (NOWRAP) return x < (int)pk;
+    return (int)((uint32_t)x - pk) < 0;
+}
+
+// One position. PUSH: candidate i enters (positions 1..n-1); the last
+// position only reads the window minimum. GENERAL: some C_i <= 0 in this
+// block, so back pops may empty the deque (see split_deque.cuh).
+template <int R, int T, bool LCAP, bool NOWRAP, bool CLAMP, bool PUSH, bool GENERAL>
+__device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, uint32_t K, uint32_t xi, int L, int Q,
+                                        uint32_t rs)
+{
+    constexpr uint32_t kStride = T * 8u;
+    constexpr uint32_t kMask = R * T * 8u - 1u;
+    if (CLAMP) {
+        d.qmax = max(d.qmax, q);
+        q = min(q, (uint32_t)Q);
+    }
+    d.pk += q * K;
+    bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe);
+    // Front pops. Reaching the back entry with it expired means a demand
+    // above Q (only possible without CLAMP): the scenario is bad, frozen
+    // with a front that never expires.
+    while (__any_sync(0xffffffffu, pf)) {
+        const bool last = d.h == d.b;
+        const uint32_t nh = (d.h + kStride) & kMask;
+        const int2 e = lds2(rs + nh);
+        if (!CLAMP && last && pf) {
+            d.frozen = true;
+            d.fx = INT32_MAX;
+            d.fe = INT32_MAX;
+            pf = false;
+        }
+        d.h = pf ? nh : d.h;
+        d.fg = pf ? e.x : d.fg;
+        d.fx = pf ? e.y : d.fx;
+        if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
+        pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe));
+    }
+    const int gi = d.fg + ci;
+    if (!PUSH) return gi;
+    const int x = (int)(d.pk + xi);               // K * (P(i) + Q) + i
+    bool pb = (d.bg >= gi) & !d.frozen;
+    if (!GENERAL) {
+        while (__any_sync(0xffffffffu, pb)) {
+            const uint32_t bp = (d.b - kStride) & kMask;
+            const int below = lds1(rs + bp);
+            d.b = pb ? bp : d.b;
+            d.bg = pb ? below : d.bg;
+            pb = pb & (below >= gi);
+        }
+        d.b = (d.b + kStride) & kMask;
+        if (d.b == d.h) {                           // the ring already held R entries
+            d.frozen = true;
+            d.fx = INT32_MAX;
+            d.fe = INT32_MAX;
+        }
+    } else {
+        bool empty = false;
+        while (__any_sync(0xffffffffu, pb)) {
+            const bool emp = d.b == d.h;
+            const uint32_t bp = (d.b - kStride) & kMask;
+            const int below = lds1(rs + bp);
+            empty |= pb & emp;
+            d.b = pb ? bp : d.b;
+            d.bg = pb ? below : d.bg;
+            pb = pb & !emp & (below >= gi);
+        }
+        d.b = (d.b + kStride) & kMask;
+        if (empty) {
+            d.h = d.b;
+            d.fg = gi;
+            d.fx = x;
+            if (LCAP) d.fe = i + L + 1;
+        } else if (d.b == d.h) {
+            d.frozen = true;
+        }
+        if (d.frozen) {                             // keep the front from ever expiring
+            d.fx = INT32_MAX;
+            d.fe = INT32_MAX;
+        }
+    }
+    sts2(rs + d.b, gi, x);
+    d.bg = gi;
+    return gi;
+}
+
+template <typename DT> struct Dem2;
+template <> struct Dem2<int16_t> { using T = unsigned short; };
+template <> struct Dem2<int32_t> { using T = unsigned int; };
+
+template <typename DT, int CAP>
+__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i)
+{
+    return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + tab.e[i - 1].x));
+}
+
+// Positions i0 .. i0 + kPrefetch - 1 (GUARD: the block may reach past n).
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
+__device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
+                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
+                                            int &out)
+{
+    constexpr bool CLAMP = sizeof(DT) == 4;
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+        const int i = i0 + u;
+        if (GUARD && i > n) break;
+        const int ci = (int)tab.e[i - 1].y;
+        const uint32_t xi = QK + (uint32_t)i;
+        if (!GUARD || i < n)
+            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs);
+        else
+            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs);
+    }
+}
+
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
+__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
+                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
+                                            int &out)
+{
+    const int m = (i0 - 1) / kPrefetch;
+    if ((tab.nonpos[m >> 5] >> (m & 31)) & 1u)
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+    else
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+}
+
+template <typename DT, bool CLAMPI, int CAP>
+__device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n,
+                                          uint32_t (&q)[kPrefetch])
+{
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u);
+}
+
+// The walk of one scenario (column s; a thread past S walks column 0 and
+// reports nothing: every lane takes part in the votes). Returns f(n) or
+// sets *aside.
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
+__device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabParam<CAP> &tab, long long s,
+                                              uint32_t rs, uint32_t slot0, bool &aside)
+{
+    const int n = p.n, Q = p.Q, L = p.L;
+    const uint32_t K = p.K;
+    const uint32_t QK = (uint32_t)Q * K;
+    const char *base = reinterpret_cast<const char *>(p.demand) + (s < p.S ? s : 0) * (long long)sizeof(DT);
+    Deque2 d;
+    d.h = d.b = slot0;
+    d.fg = d.bg = p.g0;
+    d.fx = (int)QK;                 // x(0) = K * (0 + Q) + 0
+    d.fe = L + 1;
+    d.pk = 0;
+    d.qmax = 0;
+    d.frozen = false;
+    sts2(rs + slot0, p.g0, (int)QK);
+    int out = 0;
+    uint32_t qa[kPrefetch], qb[kPrefetch];
+    prefetch2<DT, true>(base, tab, 1, n, qa);
+    int i0 = 1;
+    for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
+        prefetch2<DT, false>(base, tab, i0 + kPrefetch, n, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch, n, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, out);
+    }
+    for (; i0 <= n; i0 += 2 * kPrefetch) {
+        prefetch2<DT, true>(base, tab, i0 + kPrefetch, n, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        if (i0 + kPrefetch > n) break;
+        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch, n, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, out);
+    }
+    aside = d.frozen || d.qmax > (uint32_t)Q;
+    return out;
+}
+
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
+__global__ void __launch_bounds__(T) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
+{
+    // Rings [R][T] of (g, key) slots: thread t's slot k is at byte
+    // (k * T + t) * 8, so a warp's accesses never conflict.
+    __shared__ __align__(16) int2 rings[R * T];
+    const int tid = threadIdx.x;
+    const uint32_t rs = (uint32_t)__cvta_generic_to_shared(rings);
+    const uint32_t slot0 = (uint32_t)tid * 8u;
+    long long sum = 0;
+    // Every thread of a block runs the same number of rounds (the test is
+    // on the block's first scenario), so block-wide code after the loop is
+    // reached by all.
+    for (long long sb = (long long)blockIdx.x * T; sb < p.S; sb += p.stride) {
+        const long long s = sb + tid;
+        bool aside = false;
+        const int c = walk2_scenario<DT, R, T, LCAP, NOWRAP>(p, tab, s, rs, slot0, aside);
+        if (s < p.S) {
+            if (aside) {
+                const unsigned long long idx = atomicAdd(p.acc + ACC_OVERFLOW, 1ull);
+                p.ovf_list[idx] = (int32_t)s;
+            } else {
+                sum += c;
+                if (p.out_cost) p.out_cost[s] = c;
+            }
+        }
+    }
+    block_accumulate(sum, 0u, 0u, p.acc);
+}
+
+}  // namespace cvrpsd

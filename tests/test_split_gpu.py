@@ -18,6 +18,8 @@ pytestmark = pytest.mark.gpu
 
 INT32_MAX = 2**31 - 1
 SHAPES = [(t, s, r) for t in (64, 128, 256) for s in (1, 2) for r in (16, 32, 64)]
+# parameter-table walk: (threads, ring, rounds)
+PARAM_SHAPES = [(t, r, k) for t in (64, 128, 256) for r in (8, 16) for k in (0, 1, 3)]
 
 
 @pytest.fixture(scope="module")
@@ -112,20 +114,77 @@ def test_million_n1000_sampled(sp, cv):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"t{s[0]}_spt{s[1]}_r{s[2]}")
 def test_every_shape_int16(sp, cv, shape):
+    """Global-table walk, every shape."""
     w = workload("corr-n200", S=4099)            # ragged: not a multiple of any block
     inst = w.instances[0]
     D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 4099, dtype=np.int16)
-    sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2],
+                 variant=cv.WALK_GLOBAL_TABLE)
     check_parity(sp, inst, D)
+    assert sp.stats()["variant"] == cv.WALK_GLOBAL_TABLE
 
 
-@pytest.mark.parametrize("shape", [(128, 2, 16), (256, 2, 32), (64, 1, 64)])
-def test_shapes_int32_uncapped(sp, cv, shape):
+@pytest.mark.parametrize("shape", PARAM_SHAPES, ids=lambda s: f"t{s[0]}_r{s[1]}_rounds{s[2]}")
+def test_every_param_walk_shape_int16(sp, cv, shape):
+    """Parameter-table walk, every compiled shape, one scenario per thread or
+    several rounds of tiles per block (ragged S: the last round is partial)."""
+    w = workload("corr-n200", S=4099)
+    inst = w.instances[0]
+    D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 4099, dtype=np.int16)
+    t, r, k = shape
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=t, spt=1, ring=r, variant=cv.WALK_PARAM_TABLE, rounds=k)
+    check_parity(sp, inst, D)
+    st = sp.stats()
+    assert (st["variant"], st["threads"], st["ring"], st["rounds"]) == (cv.WALK_PARAM_TABLE, t, r, k)
+
+
+@pytest.mark.parametrize("walk", ["global", "param"])
+@pytest.mark.parametrize("shape", [(128, 2, 16), (256, 2, 32), (64, 1, 64), (128, 1, 16)])
+def test_shapes_int32_uncapped(sp, cv, shape, walk):
     w = workload("plain-n50", S=3001)
     inst = w.instances[0]
     D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 3001, dtype=np.int32)
-    sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+    v = cv.WALK_GLOBAL_TABLE if walk == "global" else cv.WALK_PARAM_TABLE
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2], variant=v, rounds=2)
     check_parity(sp, inst, D)
+    assert sp.stats()["variant"] == v
+
+
+@pytest.mark.parametrize("n, Q, L, dtype", [
+    (1025, 200, 60, np.int16),      # larger parameter table (n > 1024)
+    (4064, 150, 40, np.int16),      # the largest tour the parameter table holds
+    (1000, 2100, 1000, np.int16),   # keys that wrap: the difference test
+    (300, 40_000, 300, np.int32),   # int32 demands, keys that wrap
+    (300, 400, 20, np.int32),       # int32 demands, keys that fit
+])
+def test_param_walk_key_ranges_and_tables(sp, cv, n, Q, L, dtype):
+    inst = make_instance(n, 1, 30, seed=n + Q, Q=Q, L=L)
+    scale = max(1, Q // 200)
+    D = demand_matrix(inst.mu, inst.region, 1, n * 7 + 1, 1537, dtype=dtype)
+    if scale > 1:
+        D = (D.astype(np.int64) * scale).astype(dtype)
+    D[3, 100] = Q + 1                     # one infeasible scenario
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=128, spt=1, ring=16, variant=cv.WALK_PARAM_TABLE)
+    r, _ = check_parity(sp, inst, D)
+    assert sp.stats()["variant"] == cv.WALK_PARAM_TABLE
+    assert r.infeasible >= 1
+
+
+def test_param_walk_negative_and_too_large_int16(sp, cv):
+    """int16 demands read as unsigned: a negative one (>= 32768 as unsigned)
+    and one above Q both reach the back of the deque and freeze the walk;
+    the warp kernel classifies them (negative: an error; above Q: infeasible)."""
+    inst = make_instance(90, 1, 10, seed=5, Q=40, L=15)
+    D = demand_matrix(inst.mu, inst.region, 1, 9, 700, dtype=np.int16)
+    D[17, 3] = 41
+    D[0, 650] = 32767
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=64, spt=1, ring=8, variant=cv.WALK_PARAM_TABLE, rounds=2)
+    r, got = check_parity(sp, inst, D)
+    assert got[3] == INT32_MAX and got[650] == INT32_MAX and r.infeasible == 2
+    D[5, 200] = -1
+    with pytest.raises(cv.CvrpsdError) as e:
+        run(sp, inst, to_dev(D))
+    assert e.value.code == -5
 
 
 # ----------------------------------------------------------------- edge cases
@@ -343,9 +402,11 @@ def test_zero_break_costs_take_the_general_step(sp, cv):
     inst = instance_from_coords(coords, list(range(1, n + 1)), Q=25, L=9)
     rng = np.random.default_rng(11)
     D = rng.integers(0, 7, size=(n, 2053)).astype(np.int16)
-    for shape in [(256, 1, 16), (128, 2, 32)]:
-        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+    for shape, v in [((256, 1, 16), cv.WALK_GLOBAL_TABLE), ((128, 2, 32), cv.WALK_GLOBAL_TABLE),
+                     ((256, 1, 16), cv.WALK_PARAM_TABLE), ((128, 1, 8), cv.WALK_PARAM_TABLE)]:
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2], variant=v)
         check_parity(sp, inst, D)
+        assert sp.stats()["variant"] == v
 
 
 def test_overflow_then_back_pops_stay_bounded(sp, cv):
@@ -359,8 +420,11 @@ def test_overflow_then_back_pops_stay_bounded(sp, cv):
     inst = instance_from_coords(coords, list(range(1, n + 1)), Q=1000)
     D = np.ones((n, 300), np.int16)
     D[:, 150:] = 2
-    for shape in [(256, 1, 16), (128, 2, 16), (64, 1, 32)]:
-        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+    for shape, v in [((256, 1, 16), cv.WALK_GLOBAL_TABLE), ((128, 2, 16), cv.WALK_GLOBAL_TABLE),
+                     ((64, 1, 32), cv.WALK_GLOBAL_TABLE), ((256, 1, 16), cv.WALK_PARAM_TABLE),
+                     ((64, 1, 8), cv.WALK_PARAM_TABLE)]:
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2], variant=v)
         check_parity(sp, inst, D, Q=1000, L=n)
-        # the ray's deque peaks near 31 entries: it overflows a 16-entry ring only
-        assert (sp.stats()["overflow"] > 0) == (shape[2] == 16)
+        # the ray's deque peaks near 31 entries: it overflows rings of 8 or 16 only
+        assert sp.stats()["variant"] == v
+        assert (sp.stats()["overflow"] > 0) == (shape[2] <= 16)
