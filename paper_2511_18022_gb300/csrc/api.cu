@@ -464,7 +464,8 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
                 if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
                 goto launched;
             }
-            if (shape.ring == 8) shape.ring = 16;   // the global-table walk has rings of 16..64
+            if (shape.ring == 8 && (shape.spt != 1 || shape.threads == 64 || pred))
+                shape.ring = 16;   // rings of 8 exist for one scenario per thread, 128 or 256 threads
             if (pred && (shape.spt != 1 || shape.threads == 64 || shape.ring == 64))
                 shape = DequeShape{128, 1, 16};      // route recovery shapes
             // Vector loads of spt demands need spt-aligned rows and base.

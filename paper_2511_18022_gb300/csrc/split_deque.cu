@@ -33,6 +33,7 @@ static cudaError_t dispatch_shape(const SplitParams &p, const DequeShape &s, cud
     CVRPSD_CASE(T_, 1, 16) CVRPSD_CASE(T_, 1, 32) CVRPSD_CASE(T_, 1, 64) \
     CVRPSD_CASE(T_, 2, 16) CVRPSD_CASE(T_, 2, 32) CVRPSD_CASE(T_, 2, 64)
     CVRPSD_CASES_T(64) CVRPSD_CASES_T(128) CVRPSD_CASES_T(256)
+    CVRPSD_CASE(128, 1, 8) CVRPSD_CASE(256, 1, 8)
 #undef CVRPSD_CASES_T
 #undef CVRPSD_CASE
     return cudaErrorInvalidValue;

@@ -365,8 +365,14 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     return sum;
 }
 
+#ifndef CVRPSD_D1_TPSM
+#define CVRPSD_D1_TPSM 0
+#endif
+template <int T>
+constexpr int d1_min_blocks() { return CVRPSD_D1_TPSM > 0 ? CVRPSD_D1_TPSM / T : 1; }
+
 template <typename DT, int SPT, int R, int T, bool LCAP, bool PRED = false>
-__global__ void __launch_bounds__(T) split_deque_kernel(SplitParams p)
+__global__ void __launch_bounds__(T, d1_min_blocks<T>()) split_deque_kernel(SplitParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];   // SPT rings of R*T*8 bytes
     const int n = p.n;

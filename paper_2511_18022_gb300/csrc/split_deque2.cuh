@@ -231,8 +231,16 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     return out;
 }
 
+// Resident threads per SM the kernel is compiled for (0: the compiler's
+// choice); with a target, registers are capped at 65536 / target.
+#ifndef CVRPSD_D2_TPSM
+#define CVRPSD_D2_TPSM 0
+#endif
+template <int T>
+constexpr int d2_min_blocks() { return CVRPSD_D2_TPSM > 0 ? CVRPSD_D2_TPSM / T : 1; }
+
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
-__global__ void __launch_bounds__(T) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
+__global__ void __launch_bounds__(T, d2_min_blocks<T>()) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
 {
     // Rings [R][T] of (g, key) slots: thread t's slot k is at byte
     // (k * T + t) * 8, so a warp's accesses never conflict.
