@@ -82,7 +82,7 @@ typedef struct cvrpsd_ctx cvrpsd_ctx;
 /* Walks of the deque kernel (cvrpsd_config.variant). */
 #define CVRPSD_WALK_AUTO          0   /* PARAM_TABLE where it applies, else GLOBAL_TABLE */
 #define CVRPSD_WALK_GLOBAL_TABLE  1   /* tour table in global memory; any n, spt 1 or 2 */
-#define CVRPSD_WALK_PARAM_TABLE   2   /* tour table in the launch's parameters: n <= 4064, spt 1,
+#define CVRPSD_WALK_PARAM_TABLE   2   /* tour table in the launch's parameters: n <= 4032, spt 1,
                                          int16 demands need Q < 32768; rings of 8 or 16 */
 
 /* Launch shape of the Split. threads in {64,128,256} per block, spt

@@ -436,7 +436,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             DequeShape shape{128, 1, 16};
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
             // The parameter-table walk wherever it applies (one scenario per
-            // thread, no predecessor output, n <= 4064, ...).
+            // thread, no predecessor output, n <= 4032, ...).
             const bool v2_ok = deque2_supported(p, demand_dtype);
             const int variant = ctx->cfg.variant == CVRPSD_WALK_GLOBAL_TABLE || !v2_ok ? CVRPSD_WALK_GLOBAL_TABLE
                               : (ctx->cfg.variant == CVRPSD_WALK_PARAM_TABLE || !ctx->cfg.threads || shape.spt == 1)

@@ -13,7 +13,7 @@ namespace cvrpsd {
 // Table capacities of the kernel-parameter tour table: 8 KB for tours up to
 // 1024 customers, and the largest that fits the 32 KB parameter space.
 constexpr int kTab2Small = 1024;
-constexpr int kTab2Large = 4064;
+constexpr int kTab2Large = 4032;
 
 // Table entry of position i (index i - 1): x = byte offset of sigma_i's
 // demand row (row * pitch), y = C_i. Bit m of nonpos marks prefetch block m

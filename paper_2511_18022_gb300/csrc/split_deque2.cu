@@ -14,6 +14,9 @@ cudaError_t dispatch_deque2_general(const Walk2Params &p, const void *tab, int e
 cudaError_t dispatch_deque2_i32(const Walk2Params &p, const void *tab, bool lcap, bool nowrap, bool large,
                                 const DequeShape &s, long long grid, int *occ, cudaStream_t st);
 
+// A launch's parameters may take at most 32764 bytes.
+static_assert(sizeof(TabParam<kTab2Large>) + sizeof(Walk2Params) <= 32764, "tour table too large for the parameters");
+
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
 static cudaError_t launch2(const Walk2Params &p, const void *tab, long long grid, cudaStream_t st)
 {

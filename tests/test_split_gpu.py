@@ -152,7 +152,7 @@ def test_shapes_int32_uncapped(sp, cv, shape, walk):
 
 @pytest.mark.parametrize("n, Q, L, dtype", [
     (1025, 200, 60, np.int16),      # larger parameter table (n > 1024)
-    (4064, 150, 40, np.int16),      # the largest tour the parameter table holds
+    (4032, 150, 40, np.int16),      # the largest tour the parameter table holds
     (1000, 2100, 1000, np.int16),   # keys that wrap: the difference test
     (300, 40_000, 300, np.int32),   # int32 demands, keys that wrap
     (300, 400, 20, np.int32),       # int32 demands, keys that fit
