@@ -16,8 +16,12 @@ constexpr int kTab2Small = 1024;
 constexpr int kTab2Large = 4032;
 
 // Table entry of position i (index i - 1): x = byte offset of sigma_i's
-// demand row (row * pitch), y = C_i. Bit m of nonpos marks prefetch block m
-// (positions 1 + m * kPrefetch ...) as holding some C_i <= 0.
+// demand row (row * pitch), or with CVRPSD_D2_ROW the row itself in the low
+// bits and kTab2NoBack when no scenario can pop the deque's back at i
+// (C_{i-1} > 0 and C_i > C_{i-1}); y = C_i. Bit m of nonpos marks prefetch
+// block m (positions 1 + m * kPrefetch ...) as holding some C_i <= 0.
+constexpr uint32_t kTab2NoBack = 1u << 31;
+constexpr uint32_t kTab2RowMask = kTab2NoBack - 1u;
 template <int CAP>
 struct TabParam {
     uint2 e[CAP];
@@ -30,6 +34,8 @@ struct Walk2Params {
     long long stride;          // grid * T: scenario step between a thread's rounds
     int32_t n, Q, L, g0;       // L > n: no route-length limit
     uint32_t K;                // key scale: power of two > n
+    uint32_t pitch;            // bytes between demand rows
+    uint32_t one;              // 1 (a runtime operand of the walk's multiply-adds)
     int32_t *out_cost;         // device [S] or nullptr
     unsigned long long *acc;   // device [ACC_WORDS]
     int32_t *ovf_list;         // device [S]

@@ -105,6 +105,7 @@ DequeShape compiled_shape(const SplitParams &p, int esize, const DequeShape &s)
 bool deque2_supported(const SplitParams &p, int esize)
 {
     if (p.pred || p.n > kTab2Large || p.n < 1) return false;
+    if ((unsigned long long)p.ld * esize > 0xFFFFFFFFull) return false;   // 32-bit row pitch
     if ((unsigned long long)(p.n - 1) * (unsigned long long)p.ld * esize + (unsigned long long)p.S * esize >
         0xFFFFFFFFull)
         return false;
@@ -139,7 +140,13 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     for (size_t k = 0; k < words; ++k) nonpos[k] = 0;
     const unsigned long long pitch = (unsigned long long)p.ld * esize;
     for (int k = 0; k < p.n; ++k) {
+#if CVRPSD_D2_ROW
+        e[k].x = (uint32_t)(tab[k].row & kRowMask);
+        // position k + 1 >= 2: C_k > 0 and C_{k+1} > C_k rule out back pops
+        if (k >= 1 && tab[k - 1].c > 0 && tab[k].c > tab[k - 1].c) e[k].x |= kTab2NoBack;
+#else
         e[k].x = (uint32_t)((unsigned long long)(tab[k].row & kRowMask) * pitch);
+#endif
         e[k].y = (uint32_t)tab[k].c;
         if ((k % kPrefetch) == 0 && (tab[k].row & kRowFlagNonPositive)) {
             const int m = k / kPrefetch;
@@ -157,6 +164,8 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     w.out_cost = p.out_cost;
     w.acc = p.acc;
     w.ovf_list = p.ovf_list;
+    w.pitch = (uint32_t)pitch;
+    w.one = 1u;
     const long long tiles = (p.S + s.threads - 1) / s.threads;
     const long long grid = rounds > 0 ? (tiles + rounds - 1) / rounds : tiles;
     w.stride = grid * s.threads;

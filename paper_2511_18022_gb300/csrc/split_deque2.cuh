@@ -35,6 +35,20 @@
 #include "split_deque.cuh"
 #include "tour_table.h"
 
+// Build switches of the walk's instruction choices (0 or 1).
+#ifndef CVRPSD_D2_FRZ        // 1: a frozen scenario only sets a flag (front test carries it)
+#define CVRPSD_D2_FRZ 0
+#endif
+#ifndef CVRPSD_D2_MADD       // 1: additions as multiply-adds with a runtime 1
+#define CVRPSD_D2_MADD 0
+#endif
+#ifndef CVRPSD_D2_ROW        // 1: table holds row indexes; address = base + row * pitch
+#define CVRPSD_D2_ROW 0
+#endif
+#ifndef CVRPSD_D2_NOBACK     // 1: positions the host proves free of back pops skip the back test
+#define CVRPSD_D2_NOBACK 0
+#endif
+
 namespace cvrpsd {
 
 struct Deque2 {
@@ -48,6 +62,20 @@ struct Deque2 {
     uint32_t qmax;   // int32 demands only: largest demand seen (unsigned)
     bool frozen;     // ring overflow or a bad demand: set aside, no more pops
 };
+
+// a + c, as an integer multiply-add a * one + c with `one` a runtime 1
+// (the multiply-add pipe, not the integer ALU pipe) when CVRPSD_D2_MADD.
+__device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t c, uint32_t one)
+{
+#if CVRPSD_D2_MADD
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(c));
+    return d;
+#else
+    (void)one;
+    return a + c;
+#endif
+}
 
 // Signed capacity test of a key against K * P(i): wrapping difference, or a
 // plain compare when keys cannot wrap.
@@ -63,7 +91,7 @@ __device__ __forceinline__ bool key_expired(int x, uint32_t pk)
 // block, so back pops may empty the deque (see split_deque.cuh).
 template <int R, int T, bool LCAP, bool NOWRAP, bool CLAMP, bool PUSH, bool GENERAL>
 __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, uint32_t K, uint32_t xi, int L, int Q,
-                                        uint32_t rs)
+                                        uint32_t rs, bool noback, uint32_t one)
 {
     constexpr uint32_t kStride = T * 8u;
     constexpr uint32_t kMask = R * T * 8u - 1u;
@@ -73,44 +101,52 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     }
     d.pk += q * K;
     bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe);
+    if (CVRPSD_D2_FRZ) pf = pf & !d.frozen;
     // Front pops. Reaching the back entry with it expired means a demand
     // above Q (only possible without CLAMP): the scenario is bad, frozen
     // with a front that never expires.
     while (__any_sync(0xffffffffu, pf)) {
         const bool last = d.h == d.b;
-        const uint32_t nh = (d.h + kStride) & kMask;
+        const uint32_t nh = add2(d.h, kStride, one) & kMask;
         const int2 e = lds2(rs + nh);
         if (!CLAMP && last && pf) {
             d.frozen = true;
-            d.fx = INT32_MAX;
-            d.fe = INT32_MAX;
+            if (!CVRPSD_D2_FRZ) {
+                d.fx = INT32_MAX;
+                d.fe = INT32_MAX;
+            }
             pf = false;
         }
         d.h = pf ? nh : d.h;
         d.fg = pf ? e.x : d.fg;
         d.fx = pf ? e.y : d.fx;
-        if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
+        if (LCAP) d.fe = pf ? (int)add2((uint32_t)e.y & (K - 1), (uint32_t)(L + 1), one) : d.fe;
         pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe));
     }
-    const int gi = d.fg + ci;
+    const int gi = (int)add2((uint32_t)d.fg, (uint32_t)ci, one);
     if (!PUSH) return gi;
-    const int x = (int)(d.pk + xi);               // K * (P(i) + Q) + i
-    bool pb = (d.bg >= gi) & !d.frozen;
+    const int x = (int)add2(d.pk, xi, one);       // K * (P(i) + Q) + i
     if (!GENERAL) {
-        while (__any_sync(0xffffffffu, pb)) {
-            const uint32_t bp = (d.b - kStride) & kMask;
-            const int below = lds1(rs + bp);
-            d.b = pb ? bp : d.b;
-            d.bg = pb ? below : d.bg;
-            pb = pb & (below >= gi);
+        if (!CVRPSD_D2_NOBACK || !noback) {
+            bool pb = (d.bg >= gi) & !d.frozen;
+            while (__any_sync(0xffffffffu, pb)) {
+                const uint32_t bp = add2(d.b, 0u - kStride, one) & kMask;
+                const int below = lds1(rs + bp);
+                d.b = pb ? bp : d.b;
+                d.bg = pb ? below : d.bg;
+                pb = pb & (below >= gi);
+            }
         }
-        d.b = (d.b + kStride) & kMask;
-        if (d.b == d.h) {                           // the ring already held R entries
+        d.b = add2(d.b, kStride, one) & kMask;
+        if (CVRPSD_D2_FRZ) {
+            d.frozen |= d.b == d.h;                 // the ring already held R entries
+        } else if (d.b == d.h) {
             d.frozen = true;
             d.fx = INT32_MAX;
             d.fe = INT32_MAX;
         }
     } else {
+        bool pb = (d.bg >= gi) & !d.frozen;
         bool empty = false;
         while (__any_sync(0xffffffffu, pb)) {
             const bool emp = d.b == d.h;
@@ -130,7 +166,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         } else if (d.b == d.h) {
             d.frozen = true;
         }
-        if (d.frozen) {                             // keep the front from ever expiring
+        if (!CVRPSD_D2_FRZ && d.frozen) {           // keep the front from ever expiring
             d.fx = INT32_MAX;
             d.fe = INT32_MAX;
         }
@@ -145,49 +181,57 @@ template <> struct Dem2<int16_t> { using T = unsigned short; };
 template <> struct Dem2<int32_t> { using T = unsigned int; };
 
 template <typename DT, int CAP>
-__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i)
+__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i, uint32_t pitch)
 {
+#if CVRPSD_D2_ROW
+    const uint32_t row = tab.e[i - 1].x & kTab2RowMask;
+    return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + (unsigned long long)row * pitch));
+#else
+    (void)pitch;
     return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + tab.e[i - 1].x));
+#endif
 }
 
 // Positions i0 .. i0 + kPrefetch - 1 (GUARD: the block may reach past n).
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
 __device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
-                                            int &out)
+                                            uint32_t one, int &out)
 {
     constexpr bool CLAMP = sizeof(DT) == 4;
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = i0 + u;
         if (GUARD && i > n) break;
-        const int ci = (int)tab.e[i - 1].y;
+        const uint2 e = tab.e[i - 1];
+        const int ci = (int)e.y;
+        const bool noback = CVRPSD_D2_NOBACK && (e.x & kTab2NoBack) != 0;
         const uint32_t xi = QK + (uint32_t)i;
         if (!GUARD || i < n)
-            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs);
+            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback, one);
         else
-            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs);
+            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback, one);
     }
 }
 
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
 __device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
-                                            int &out)
+                                            uint32_t one, int &out)
 {
     const int m = (i0 - 1) / kPrefetch;
     if ((tab.nonpos[m >> 5] >> (m & 31)) & 1u)
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, one, out);
     else
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, one, out);
 }
 
 template <typename DT, bool CLAMPI, int CAP>
-__device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n,
+__device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n, uint32_t pitch,
                                           uint32_t (&q)[kPrefetch])
 {
 #pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u);
+    for (int u = 0; u < kPrefetch; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u, pitch);
 }
 
 // The walk of one scenario (column s; a thread past S walks column 0 and
@@ -212,20 +256,21 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     sts2(rs + slot0, p.g0, (int)QK);
     int out = 0;
     uint32_t qa[kPrefetch], qb[kPrefetch];
-    prefetch2<DT, true>(base, tab, 1, n, qa);
+    const uint32_t one = p.one, pitch = p.pitch;
+    prefetch2<DT, true>(base, tab, 1, n, pitch, qa);
     int i0 = 1;
     for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
-        prefetch2<DT, false>(base, tab, i0 + kPrefetch, n, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
-        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch, n, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, out);
+        prefetch2<DT, false>(base, tab, i0 + kPrefetch, n, pitch, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, one, out);
+        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch, n, pitch, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, one, out);
     }
     for (; i0 <= n; i0 += 2 * kPrefetch) {
-        prefetch2<DT, true>(base, tab, i0 + kPrefetch, n, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        prefetch2<DT, true>(base, tab, i0 + kPrefetch, n, pitch, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, one, out);
         if (i0 + kPrefetch > n) break;
-        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch, n, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, out);
+        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch, n, pitch, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, one, out);
     }
     aside = d.frozen || d.qmax > (uint32_t)Q;
     return out;
