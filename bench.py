@@ -39,6 +39,9 @@ METRIC = "Split scenario·customer relaxations/s at n=1000,S=2^20 (bit-exact); %
 UNIT = "cells/s"
 KERNEL_FILES = ["paper_2511_18022_gb300/csrc/split_deque.cuh",
                 "paper_2511_18022_gb300/csrc/split_deque.cu",
+                "paper_2511_18022_gb300/csrc/split_deque2.cuh",
+                "paper_2511_18022_gb300/csrc/split_deque2.cu",
+                "paper_2511_18022_gb300/csrc/deque2.h",
                 "paper_2511_18022_gb300/csrc/kernels.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_deque_million-n1000.traffic.json")
 
@@ -267,8 +270,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     tuned = None
     if args.shape:
-        t, s, r = (int(x) for x in args.shape.split(","))
-        sp.configure(kernel=cv.KERNEL_DEQUE, threads=t, spt=s, ring=r)
+        t, s, r, *v = (int(x) for x in args.shape.split(","))
+        sp.configure(kernel=cv.KERNEL_DEQUE, threads=t, spt=s, ring=r, variant=v[0] if v else 0)
     elif not args.no_tune:
         tuned = sp.autotune(inst.tour, inst.dist, D, inst.Q, inst.L)
 
@@ -372,7 +375,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
             "data": "synthetic", "config": workload_config(w, inst) | {
-                "kernel": f"deque threads={st['threads']} spt={st['spt']} ring={st['ring']}",
+                "kernel": (f"deque walk={'parameter-table' if st['variant'] == 2 else 'global-table'} "
+                           f"threads={st['threads']} spt={st['spt']} ring={st['ring']}"),
                 "shape_source": "fixed" if args.shape else ("autotuned" if tuned else "library default"),
                 "parallelism": (f"scenario shards x{world} of one {S_total}-scenario set, one int64 "
                                 f"all-reduce (NCCL) of the SAA per step") if world > 1 else "one GPU"},
@@ -401,7 +405,7 @@ def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_ce
     peak, peak_kind = peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
     traffic, winst = None, None
-    shape = f"{st['threads']},{st['spt']},{st['ring']}"
+    shape = f"{st['threads']},{st['spt']},{st['ring']},walk{st['variant']}"
     try:
         t = json.load(open(TRAFFIC_FILE))
         if t.get("kernel_hash") == kernel_hash() and S == (1 << 20):
@@ -413,7 +417,8 @@ def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_ce
            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": algo_bytes,
            "floor_ms": round(algo_bytes / (peak * 1e9) * 1e3, 4)}
     roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": peak, "unit": "GB/s", "frac": hbm["frac"],
-            "traffic": traffic, "peak_kind": peak_kind, "kernel": "split_deque_kernel",
+            "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "split_deque2_kernel" if st["variant"] == 2 else "split_deque_kernel",
             "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes": algo_bytes, "hbm": hbm}
     if relax_per_cell is not None and int_ops:
         ops_per_cell = relax_per_cell + 6.0
@@ -690,7 +695,8 @@ def main():
     ap.add_argument("--S", type=int, default=0,
                     help="scenarios per rank (default: the workload's own); a smaller S gives a "
                          "scaled-down case of the same generator, e.g. for ncu captures")
-    ap.add_argument("--shape", default="", help="threads,spt,ring of the deque kernel")
+    ap.add_argument("--shape", default="", help="threads,spt,ring[,walk] of the deque kernel (walk 1: global "
+                                                "table, 2: parameter table, default: automatic)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-cols", type=int, default=8192)

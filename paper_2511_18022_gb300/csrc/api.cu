@@ -446,8 +446,9 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
                 if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
                 DequeShape ran{};
                 const int rounds = ctx->cfg.rounds;
-                CK(launch_split_deque2(p, ctx->h_tab, demand_dtype, DequeShape{shape.threads, 1, shape.ring}, rounds,
-                                       &ran, stream),
+                // untuned default: 256 threads, rings of 8 (fastest on GB300 at full size)
+                const DequeShape want = ctx->cfg.threads ? DequeShape{shape.threads, 1, shape.ring} : DequeShape{256, 1, 8};
+                CK(launch_split_deque2(p, ctx->h_tab, demand_dtype, want, rounds, &ran, stream),
                    "split_deque2 launch");
                 if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
                 st.kernel = CVRPSD_KERNEL_DEQUE;
@@ -657,9 +658,9 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     best.best_ms = 1e30f;
     int timed = 0;
     // Candidates: the parameter-table walk (where it applies) over threads x
-    // ring x rounds (one scenario per thread, or the fewest whole rounds the
-    // resident grid allows and one more), then the global-table walk over
-    // threads x spt x ring.
+    // ring, one scenario per thread (grids of several rounds per block
+    // measured slower on GB300 and are not swept), then the global-table walk
+    // over threads x spt x ring.
     std::vector<cvrpsd_config> cands;
     SplitParams probe{};
     probe.n = n;
@@ -670,19 +671,8 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
     probe.K = key_scale(n);
     if (deque2_supported(probe, demand_dtype)) {
         for (int threads : {64, 128, 256})
-            for (int ring : {8, 16}) {
-                const int occ = deque2_blocks_per_sm(probe, demand_dtype, DequeShape{threads, 1, ring});
-                const long long tiles = (S + threads - 1) / threads;
-                const long long resident = (long long)occ * (ctx->sm_count > 0 ? ctx->sm_count : 1);
-                const int r_min = resident > 0 ? (int)std::min<long long>((tiles + resident - 1) / resident, 1024) : 0;
+            for (int ring : {8, 16})
                 cands.push_back(cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, 0});
-                if (r_min >= 1) {
-                    cands.push_back(cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, r_min});
-                    if (r_min < 1024)
-                        cands.push_back(
-                            cvrpsd_config{CVRPSD_KERNEL_DEQUE, threads, 1, ring, CVRPSD_WALK_PARAM_TABLE, r_min + 1});
-                }
-            }
     }
     for (int threads : {64, 128, 256})
         for (int spt : {1, 2})

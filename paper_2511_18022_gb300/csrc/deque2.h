@@ -15,17 +15,23 @@ namespace cvrpsd {
 constexpr int kTab2Small = 1024;
 constexpr int kTab2Large = 4032;
 
-// Table entry of position i (index i - 1): x = byte offset of sigma_i's
-// demand row (row * pitch), or with CVRPSD_D2_ROW the row itself in the low
-// bits and kTab2NoBack when no scenario can pop the deque's back at i
-// (C_{i-1} > 0 and C_i > C_{i-1}); y = C_i. Bit m of nonpos marks prefetch
-// block m (positions 1 + m * kPrefetch ...) as holding some C_i <= 0.
+// Tour positions per prefetch block of the second walk: its demands are
+// loaded one block ahead (at full occupancy four positions hide the load
+// latency, and the walk then fits 32 registers).
+constexpr int kPrefetch2 = 4;
+
+// Table entry of position i (index i - 1): x = the demand row of sigma_i in
+// the low bits, plus kTab2NoBack when no scenario can pop the deque's back
+// at i (C_{i-1} > 0 and C_i > C_{i-1}, see split_deque2.cuh); y = C_i. Bit m
+// of nonpos marks prefetch block m (positions 1 + m * kPrefetch2 ...) as
+// holding some C_i <= 0 with i < n.
 constexpr uint32_t kTab2NoBack = 1u << 31;
 constexpr uint32_t kTab2RowMask = kTab2NoBack - 1u;
+
 template <int CAP>
 struct TabParam {
     uint2 e[CAP];
-    uint32_t nonpos[(CAP / kPrefetch + 31) / 32];
+    uint32_t nonpos[(CAP / kPrefetch2 + 31) / 32];
 };
 
 struct Walk2Params {
@@ -35,7 +41,6 @@ struct Walk2Params {
     int32_t n, Q, L, g0;       // L > n: no route-length limit
     uint32_t K;                // key scale: power of two > n
     uint32_t pitch;            // bytes between demand rows
-    uint32_t one;              // 1 (a runtime operand of the walk's multiply-adds)
     int32_t *out_cost;         // device [S] or nullptr
     unsigned long long *acc;   // device [ACC_WORDS]
     int32_t *ovf_list;         // device [S]
@@ -53,9 +58,5 @@ bool deque2_supported(const SplitParams &p, int esize);
 // T scenarios. *shape_ran receives the (threads, ring) actually launched.
 cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int esize, const DequeShape &shape,
                                 int rounds, DequeShape *shape_ran, cudaStream_t stream);
-
-// Blocks of `shape` resident per SM for this Split's kernel class (0 if the
-// class or shape is not compiled).
-int deque2_blocks_per_sm(const SplitParams &p, int esize, const DequeShape &shape);
 
 }  // namespace cvrpsd

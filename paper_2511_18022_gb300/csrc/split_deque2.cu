@@ -112,18 +112,6 @@ bool deque2_supported(const SplitParams &p, int esize)
     return esize == 4 || p.Q < 32768;
 }
 
-int deque2_blocks_per_sm(const SplitParams &p, int esize, const DequeShape &shape)
-{
-    int occ = 0;
-    Walk2Params w{};
-    const DequeShape s = compiled_shape(p, esize, shape);
-    if (route(w, nullptr, p, esize, s, 0, &occ, nullptr) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return occ;
-}
-
 cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int esize, const DequeShape &shape,
                                 int rounds, DequeShape *shape_ran, cudaStream_t stream)
 {
@@ -140,16 +128,13 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     for (size_t k = 0; k < words; ++k) nonpos[k] = 0;
     const unsigned long long pitch = (unsigned long long)p.ld * esize;
     for (int k = 0; k < p.n; ++k) {
-#if CVRPSD_D2_ROW
         e[k].x = (uint32_t)(tab[k].row & kRowMask);
-        // position k + 1 >= 2: C_k > 0 and C_{k+1} > C_k rule out back pops
-        if (k >= 1 && tab[k - 1].c > 0 && tab[k].c > tab[k - 1].c) e[k].x |= kTab2NoBack;
-#else
-        e[k].x = (uint32_t)((unsigned long long)(tab[k].row & kRowMask) * pitch);
-#endif
         e[k].y = (uint32_t)tab[k].c;
-        if ((k % kPrefetch) == 0 && (tab[k].row & kRowFlagNonPositive)) {
-            const int m = k / kPrefetch;
+        // Position k + 1 >= 2 with C_k > 0 and C_{k+1} > C_k: no back pops.
+        if (k >= 1 && tab[k - 1].c > 0 && tab[k].c > tab[k - 1].c) e[k].x |= kTab2NoBack;
+        // C_{k+1} <= 0 (k + 1 < n) marks its prefetch block.
+        if (k + 1 < p.n && tab[k].c <= 0) {
+            const int m = k / kPrefetch2;
             nonpos[m >> 5] |= 1u << (m & 31);
         }
     }
@@ -165,7 +150,6 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     w.acc = p.acc;
     w.ovf_list = p.ovf_list;
     w.pitch = (uint32_t)pitch;
-    w.one = 1u;
     const long long tiles = (p.S + s.threads - 1) / s.threads;
     const long long grid = rounds > 0 ? (tiles + rounds - 1) / rounds : tiles;
     w.stride = grid * s.threads;

@@ -1,12 +1,14 @@
 // Scenario-parallel Split, second walk: the same monotone-deque recursion as
 // split_deque.cuh (one thread per scenario, Section 3's scenario level;
-// Eq. 1-3 through the separable segment cost, see there), with the fixed
-// per-position work cut down:
+// Eq. 1-3 through the separable segment cost, see there), with less fixed
+// work per position. The walk is bound by instruction issue and by the
+// integer ALU pipe (compares, selects, logic, which that pipe executes at
+// half the issue rate), so every change below removes instructions from one
+// of the two:
 //
 //  - The tour table is a kernel parameter (__grid_constant__), read at a
-//    block-uniform index: one constant-bank load per position gives the
-//    demand row's byte offset (pre-multiplied by the row pitch) and C_i, so
-//    the demand address is one add and no global table load is issued.
+//    block-uniform index from the constant bank: no global table loads, and
+//    the demand address is one wide multiply-add (row * pitch + column).
 //  - int16 demands are read as unsigned 16-bit values. A demand above Q (a
 //    negative one reads as >= 32768 > Q) expires every deque entry, the back
 //    one included; the front walk notices when it would pass the back,
@@ -14,15 +16,17 @@
 //    running maximum of the first walk are gone (int32 demands keep them).
 //  - When n * Q * K + (Q + 1) * K + n < 2^31 (checked on the host), keys
 //    never wrap and the capacity test is one signed compare (NOWRAP).
-//  - A frozen scenario (ring overflow or a bad demand) gets a front that can
-//    never expire (key and expiry at INT_MAX) and is excluded from back
-//    pops, so the per-position tests carry no freeze term.
-//  - The rings are a static shared array, so a slot's address is its masked
-//    byte offset plus a constant the loads and stores fold in.
+//  - A frozen scenario (ring overflow or a bad demand) only sets a flag that
+//    the front and back tests carry.
+//  - Where C_{i-1} > 0 and C_i > C_{i-1}, no scenario can pop the deque's
+//    back at position i (dq2_step gives the argument); the host marks those
+//    positions and the walk skips the back test and its vote there.
+//  - The rings are a static shared array (a slot's address is its masked
+//    byte offset plus a constant), and with rings of 8 entries and 32
+//    registers per thread the SM holds 2048 threads of the walk.
 //  - The grid may be smaller than one thread per scenario: a thread then
 //    walks scenarios s, s + G*T, ... (every thread of a block the same
-//    number of times), which lets the host make the number of rounds an
-//    integer and avoid a part-empty last wave.
+//    number of times).
 //
 // Set-aside scenarios (ring too small, a demand above Q, a negative demand)
 // go to the warp kernel exactly as before.
@@ -34,20 +38,6 @@
 #include "kernels.h"
 #include "split_deque.cuh"
 #include "tour_table.h"
-
-// Build switches of the walk's instruction choices (0 or 1).
-#ifndef CVRPSD_D2_FRZ        // 1: a frozen scenario only sets a flag (front test carries it)
-#define CVRPSD_D2_FRZ 0
-#endif
-#ifndef CVRPSD_D2_MADD       // 1: additions as multiply-adds with a runtime 1
-#define CVRPSD_D2_MADD 0
-#endif
-#ifndef CVRPSD_D2_ROW        // 1: table holds row indexes; address = base + row * pitch
-#define CVRPSD_D2_ROW 0
-#endif
-#ifndef CVRPSD_D2_NOBACK     // 1: positions the host proves free of back pops skip the back test
-#define CVRPSD_D2_NOBACK 0
-#endif
 
 namespace cvrpsd {
 
@@ -63,20 +53,6 @@ struct Deque2 {
     bool frozen;     // ring overflow or a bad demand: set aside, no more pops
 };
 
-// a + c, as an integer multiply-add a * one + c with `one` a runtime 1
-// (the multiply-add pipe, not the integer ALU pipe) when CVRPSD_D2_MADD.
-__device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t c, uint32_t one)
-{
-#if CVRPSD_D2_MADD
-    uint32_t d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(c));
-    return d;
-#else
-    (void)one;
-    return a + c;
-#endif
-}
-
 // Signed capacity test of a key against K * P(i): wrapping difference, or a
 // plain compare when keys cannot wrap.
 template <bool NOWRAP>
@@ -91,7 +67,7 @@ __device__ __forceinline__ bool key_expired(int x, uint32_t pk)
 // block, so back pops may empty the deque (see split_deque.cuh).
 template <int R, int T, bool LCAP, bool NOWRAP, bool CLAMP, bool PUSH, bool GENERAL>
 __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, uint32_t K, uint32_t xi, int L, int Q,
-                                        uint32_t rs, bool noback, uint32_t one)
+                                        uint32_t rs, bool noback)
 {
     constexpr uint32_t kStride = T * 8u;
     constexpr uint32_t kMask = R * T * 8u - 1u;
@@ -101,50 +77,40 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     }
     d.pk += q * K;
     bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe);
-    if (CVRPSD_D2_FRZ) pf = pf & !d.frozen;
+    pf = pf & !d.frozen;
     // Front pops. Reaching the back entry with it expired means a demand
     // above Q (only possible without CLAMP): the scenario is bad, frozen
     // with a front that never expires.
     while (__any_sync(0xffffffffu, pf)) {
         const bool last = d.h == d.b;
-        const uint32_t nh = add2(d.h, kStride, one) & kMask;
+        const uint32_t nh = (d.h + kStride) & kMask;
         const int2 e = lds2(rs + nh);
         if (!CLAMP && last && pf) {
             d.frozen = true;
-            if (!CVRPSD_D2_FRZ) {
-                d.fx = INT32_MAX;
-                d.fe = INT32_MAX;
-            }
             pf = false;
         }
         d.h = pf ? nh : d.h;
         d.fg = pf ? e.x : d.fg;
         d.fx = pf ? e.y : d.fx;
-        if (LCAP) d.fe = pf ? (int)add2((uint32_t)e.y & (K - 1), (uint32_t)(L + 1), one) : d.fe;
+        if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
         pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe));
     }
-    const int gi = (int)add2((uint32_t)d.fg, (uint32_t)ci, one);
+    const int gi = d.fg + ci;
     if (!PUSH) return gi;
-    const int x = (int)add2(d.pk, xi, one);       // K * (P(i) + Q) + i
+    const int x = (int)(d.pk + xi);       // K * (P(i) + Q) + i
     if (!GENERAL) {
-        if (!CVRPSD_D2_NOBACK || !noback) {
+        if (!noback) {
             bool pb = (d.bg >= gi) & !d.frozen;
             while (__any_sync(0xffffffffu, pb)) {
-                const uint32_t bp = add2(d.b, 0u - kStride, one) & kMask;
+                const uint32_t bp = (d.b - kStride) & kMask;
                 const int below = lds1(rs + bp);
                 d.b = pb ? bp : d.b;
                 d.bg = pb ? below : d.bg;
                 pb = pb & (below >= gi);
             }
         }
-        d.b = add2(d.b, kStride, one) & kMask;
-        if (CVRPSD_D2_FRZ) {
-            d.frozen |= d.b == d.h;                 // the ring already held R entries
-        } else if (d.b == d.h) {
-            d.frozen = true;
-            d.fx = INT32_MAX;
-            d.fe = INT32_MAX;
-        }
+        d.b = (d.b + kStride) & kMask;
+        d.frozen |= d.b == d.h;                     // the ring already held R entries
     } else {
         bool pb = (d.bg >= gi) & !d.frozen;
         bool empty = false;
@@ -163,12 +129,8 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
             d.fg = gi;
             d.fx = x;
             if (LCAP) d.fe = i + L + 1;
-        } else if (d.b == d.h) {
-            d.frozen = true;
-        }
-        if (!CVRPSD_D2_FRZ && d.frozen) {           // keep the front from ever expiring
-            d.fx = INT32_MAX;
-            d.fe = INT32_MAX;
+        } else {
+            d.frozen |= d.b == d.h;
         }
     }
     sts2(rs + d.b, gi, x);
@@ -183,55 +145,48 @@ template <> struct Dem2<int32_t> { using T = unsigned int; };
 template <typename DT, int CAP>
 __device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i, uint32_t pitch)
 {
-#if CVRPSD_D2_ROW
     const uint32_t row = tab.e[i - 1].x & kTab2RowMask;
     return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + (unsigned long long)row * pitch));
-#else
-    (void)pitch;
-    return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + tab.e[i - 1].x));
-#endif
 }
 
-// Positions i0 .. i0 + kPrefetch - 1 (GUARD: the block may reach past n).
+// Positions i0 .. i0 + kPrefetch2 - 1 (GUARD: the block may reach past n).
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
-__device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
-                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
-                                            uint32_t one, int &out)
+__device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
+                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
 {
     constexpr bool CLAMP = sizeof(DT) == 4;
 #pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) {
+    for (int u = 0; u < kPrefetch2; ++u) {
         const int i = i0 + u;
         if (GUARD && i > n) break;
         const uint2 e = tab.e[i - 1];
         const int ci = (int)e.y;
-        const bool noback = CVRPSD_D2_NOBACK && (e.x & kTab2NoBack) != 0;
+        const bool noback = (e.x & kTab2NoBack) != 0;
         const uint32_t xi = QK + (uint32_t)i;
         if (!GUARD || i < n)
-            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback, one);
+            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
         else
-            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback, one);
+            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
     }
 }
 
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
-__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch], const TabParam<CAP> &tab,
-                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
-                                            uint32_t one, int &out)
+__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
+                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
 {
-    const int m = (i0 - 1) / kPrefetch;
+    const int m = (i0 - 1) / kPrefetch2;
     if ((tab.nonpos[m >> 5] >> (m & 31)) & 1u)
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, one, out);
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
     else
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, one, out);
+        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
 }
 
 template <typename DT, bool CLAMPI, int CAP>
 __device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n, uint32_t pitch,
-                                          uint32_t (&q)[kPrefetch])
+                                          uint32_t (&q)[kPrefetch2])
 {
 #pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u, pitch);
+    for (int u = 0; u < kPrefetch2; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u, pitch);
 }
 
 // The walk of one scenario (column s; a thread past S walks column 0 and
@@ -255,34 +210,34 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     d.frozen = false;
     sts2(rs + slot0, p.g0, (int)QK);
     int out = 0;
-    uint32_t qa[kPrefetch], qb[kPrefetch];
-    const uint32_t one = p.one, pitch = p.pitch;
+    uint32_t qa[kPrefetch2], qb[kPrefetch2];
+    const uint32_t pitch = p.pitch;
     prefetch2<DT, true>(base, tab, 1, n, pitch, qa);
     int i0 = 1;
-    for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
-        prefetch2<DT, false>(base, tab, i0 + kPrefetch, n, pitch, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, one, out);
-        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch, n, pitch, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, one, out);
+    for (; i0 + 3 * kPrefetch2 - 1 < n; i0 += 2 * kPrefetch2) {
+        prefetch2<DT, false>(base, tab, i0 + kPrefetch2, n, pitch, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch2, n, pitch, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
     }
-    for (; i0 <= n; i0 += 2 * kPrefetch) {
-        prefetch2<DT, true>(base, tab, i0 + kPrefetch, n, pitch, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, one, out);
-        if (i0 + kPrefetch > n) break;
-        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch, n, pitch, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, rs, one, out);
+    for (; i0 <= n; i0 += 2 * kPrefetch2) {
+        prefetch2<DT, true>(base, tab, i0 + kPrefetch2, n, pitch, qb);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        if (i0 + kPrefetch2 > n) break;
+        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch2, n, pitch, qa);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
     }
     aside = d.frozen || d.qmax > (uint32_t)Q;
     return out;
 }
 
-// Resident threads per SM the kernel is compiled for (0: the compiler's
-// choice); with a target, registers are capped at 65536 / target.
-#ifndef CVRPSD_D2_TPSM
-#define CVRPSD_D2_TPSM 0
-#endif
+// The walk is compiled for 2048 resident threads per SM (the most an SM
+// holds): 32 registers a thread, and with rings of 8 its blocks fit the
+// shared memory too. Full occupancy measured 4 % faster than the compiler's
+// own choice (40 registers, 12 blocks of 128).
+constexpr int kD2ThreadsPerSM = 2048;
 template <int T>
-constexpr int d2_min_blocks() { return CVRPSD_D2_TPSM > 0 ? CVRPSD_D2_TPSM / T : 1; }
+constexpr int d2_min_blocks() { return kD2ThreadsPerSM / T; }
 
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
 __global__ void __launch_bounds__(T, d2_min_blocks<T>()) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
