@@ -409,8 +409,9 @@ def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_ce
     try:
         t = json.load(open(TRAFFIC_FILE))
         if t.get("kernel_hash") == kernel_hash() and S == (1 << 20):
-            traffic = t["shapes"].get(shape)
-            winst = t.get("inst_executed", {}).get(shape)
+            walk = f"walk{st['variant']}"
+            traffic = t["shapes"].get(shape) or t.get("walks", {}).get(walk)
+            winst = t.get("inst_executed", {}).get(shape) or t.get("walks_inst_executed", {}).get(walk)
     except Exception:
         pass
     hbm = {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -442,6 +443,7 @@ def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_ce
         roof["issue"] = {"achieved": round(iach / 1e9, 1), "peak": round(ipeak / 1e9, 1),
                          "unit": "G warp-instructions/s", "frac": round(iach / ipeak, 4),
                          "warp_instructions_per_launch": winst,
+                         "counts_shape": shape if shape in t.get("inst_executed", {}) else "256,1,8,walk2",
                          "per_warp_position": round(winst / (S / 32 * n), 2)}
     return roof
 

@@ -437,7 +437,9 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
             // The parameter-table walk wherever it applies (one scenario per
             // thread, no predecessor output, n <= 4032, ...).
-            const bool v2_ok = deque2_supported(p, demand_dtype);
+            // Host buffers keep the global-table walk: its prefetch runs twice
+            // as far ahead, which the host link's latency wants.
+            const bool v2_ok = deque2_supported(p, demand_dtype) && !host_buffers;
             const int variant = ctx->cfg.variant == CVRPSD_WALK_GLOBAL_TABLE || !v2_ok ? CVRPSD_WALK_GLOBAL_TABLE
                               : (ctx->cfg.variant == CVRPSD_WALK_PARAM_TABLE || !ctx->cfg.threads || shape.spt == 1)
                                   ? CVRPSD_WALK_PARAM_TABLE
@@ -465,6 +467,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
                 if (timed) CK(cudaEventRecord(ctx->ev_t[2], stream), "cudaEventRecord");
                 goto launched;
             }
+            if (host_buffers && !ctx->cfg.threads) shape = DequeShape{128, 1, 16};
             if (shape.ring == 8 && (shape.spt != 1 || shape.threads == 64 || pred))
                 shape.ring = 16;   // rings of 8 exist for one scenario per thread, 128 or 256 threads
             if (pred && (shape.spt != 1 || shape.threads == 64 || shape.ring == 64))
