@@ -558,16 +558,29 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     start = np.random.default_rng(1234).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
-    plain = search.LocalSearch(sp.ctx, inst, D, start, k=64, seed=99)
-    for _ in range(args.warmup):
-        plain.step()
-    plain = search.LocalSearch(sp.ctx, inst, D, start, k=64, seed=99)
+    M, k = 4096, 64
+    # warm-up on a copy (first launches, allocations)
+    search.LocalSearch(sp.ctx, inst, D, start, M=M, seed=1, exact_all=True).run(max(args.warmup, 1))
+    search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=1, scale=scale).run(
+        max(args.warmup, 1))
+    # plain-Split search: every one of the M neighbours split exactly
+    plain = search.LocalSearch(sp.ctx, inst, D, start, M=M, seed=99, exact_all=True)
     plog = plain.run(args.steps)
-    screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=4096, k=64, seed=99,
+    # screened search, same moves: equal iterations, then equal wall time
+    screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99,
                                   retrain_every=25, scale=scale)
     slog = screened.run(args.steps)
-    gap = (screened.cur_cost - plain.cur_cost) / plain.cur_cost
+    timed = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99,
+                               retrain_every=25, scale=scale)
+    tlog = timed.run(1_000_000, seconds=plog.seconds)
+    # the old baseline: k random neighbours split exactly
+    rand = search.LocalSearch(sp.ctx, inst, D, start, k=k, seed=99)
+    rlog = rand.run(args.steps)
+    quality = [search.neighbourhood_quality(sp.ctx, inst, D, sur, scale, t, M=M, k=k, seed=17 + j)
+               for j, t in enumerate([start, plain.cur.cpu().numpy(), screened.cur.cpu().numpy()])]
     if rank == 0:
+        gap_it = (screened.cur_cost - plain.cur_cost) / plain.cur_cost
+        gap_t = (timed.cur_cost - plain.cur_cost) / plain.cur_cost
         print(json.dumps({
             "metric": "surrogate-screened local search: candidate tours/s (exact Split on the top 64 of 4096)",
             "value": slog.candidates_per_s, "unit": "tours/s", "n_gpus": world, "steps": args.steps,
@@ -575,14 +588,26 @@ def run_surrogate(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, fp32 accumulation; i32 Split",
             "data": "synthetic",
             "config": {"workload": w.name, "n": inst.n, "S": S, "Q": inst.Q, "L": inst.L,
-                       "train_pairs": args.train_pairs, "epochs": args.epochs, "screen": 4096, "exact": 64},
-            "plain": {"candidate_tours_per_s": plog.candidates_per_s, "final_saa_cost": plain.cur_cost,
-                      "ms_per_iteration": plog.seconds / args.steps * 1e3},
-            "surrogate": {"candidate_tours_per_s": slog.candidates_per_s, "final_saa_cost": screened.cur_cost,
-                          "holdout_mae": mae, "cost_sd": float(costs.std().item()),
-                          "label_seconds": t_label, "train_seconds": t_train},
+                       "train_pairs": args.train_pairs, "epochs": args.epochs, "screen": M, "exact": k},
+            "plain_split_search": {"what": f"all {M} neighbours split exactly per iteration, same moves",
+                                   "candidate_tours_per_s": plog.candidates_per_s,
+                                   "final_saa_cost": plain.cur_cost, "iterations": args.steps,
+                                   "ms_per_iteration": plog.seconds / args.steps * 1e3},
+            "screened_equal_iterations": {"final_saa_cost": screened.cur_cost, "iterations": args.steps,
+                                          "gap_vs_plain": gap_it,
+                                          "ms_per_iteration": slog.seconds / args.steps * 1e3},
+            "screened_equal_time": {"final_saa_cost": timed.cur_cost, "iterations": timed.iterations,
+                                    "seconds": tlog.seconds, "gap_vs_plain": gap_t},
+            "random_k_search": {"what": f"{k} random neighbours split exactly per iteration",
+                                "final_saa_cost": rand.cur_cost,
+                                "ms_per_iteration": rlog.seconds / args.steps * 1e3},
             "speedup_candidates": slog.candidates_per_s / plog.candidates_per_s,
-            "final_cost_gap": gap,
+            "surrogate": {"holdout_mae": mae, "training_cost_sd": float(costs.std().item()),
+                          "label_seconds": t_label, "train_seconds": t_train,
+                          "neighbourhoods": quality,
+                          "mean_spearman": float(np.mean([q["spearman"] for q in quality])),
+                          "mean_recall_at_k": float(np.mean([q["recall_at_k"] for q in quality])),
+                          "mean_mae": float(np.mean([q["mae"] for q in quality]))},
             "gpu_launches": None,
         }))
     sur.close()

@@ -208,6 +208,7 @@ int cvrpsd_destroy(cvrpsd_ctx *ctx)
     if (ctx->h_gen) cudaFreeHost(ctx->h_gen);
     if (ctx->ev_tab) cudaEventDestroy(ctx->ev_tab);
     if (ctx->ev_gen) cudaEventDestroy(ctx->ev_gen);
+    if (ctx->ev_dist) cudaEventDestroy(ctx->ev_dist);
     for (cudaEvent_t e : ctx->ev_t)
         if (e) cudaEventDestroy(e);
     if (ctx->mt_tabs) cudaFree(ctx->mt_tabs);
@@ -215,6 +216,7 @@ int cvrpsd_destroy(cvrpsd_ctx *ctx)
     if (ctx->mt_acc) cudaFree(ctx->mt_acc);
     if (ctx->mt_list) cudaFree(ctx->mt_list);
     if (ctx->mt_dist) cudaFree(ctx->mt_dist);
+    if (ctx->mt_dist_host) cudaFreeHost(ctx->mt_dist_host);
     if (ctx->seq_lo) cudaFree(ctx->seq_lo);
     if (ctx->seq_flags) cudaFree(ctx->seq_flags);
     if (ctx->seq_mats) cudaFree(ctx->seq_mats);

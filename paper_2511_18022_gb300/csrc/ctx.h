@@ -42,6 +42,11 @@ struct cvrpsd_ctx {
     long long mt_list_cap = 0;
     int32_t *mt_dist = nullptr;
     long long mt_dist_cap = 0;
+    int32_t *mt_dist_host = nullptr;       // pinned staging copy of the last distances uploaded
+    long long mt_dist_host_cap = 0;
+    unsigned long long mt_dist_key = 0;    // hash of those distances (with n); 0 = none
+    int mt_dist_n = 0;
+    cudaEvent_t ev_dist = nullptr;         // their upload done (the pinned copy is free again)
     // sequence-parallel Split scratch
     int32_t *seq_lo = nullptr;
     long long seq_lo_cap = 0;

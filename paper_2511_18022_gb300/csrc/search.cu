@@ -137,7 +137,7 @@ cudaError_t launch_tour_means(const unsigned long long *acc, int T, long long S,
     return cudaGetLastError();
 }
 
-// k smallest scores (ties: smaller index first) of M <= 8192, one block:
+// k smallest scores (ties: smaller index first) of M <= 16384, one block:
 // bitonic sort of (score, index) pairs padded to a power of two.
 __global__ void topk_kernel(const float *scores, int M, int k, int32_t *idx_out)
 {

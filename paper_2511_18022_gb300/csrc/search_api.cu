@@ -77,13 +77,19 @@ int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, 
         (d_infeasible && !is_device_ptr(d_infeasible, ctx->device)))
         return fail(ctx, CVRPSD_ERR_ARG, "outputs must be device memory");
     if (L > n) L = n;
-    // Bounds that hold for every tour of this instance.
+    // Bounds that hold for every tour of this instance, and a hash of the
+    // matrix (FNV-1a over its words) in the same pass: a search calls this
+    // every iteration with the same distances, which are then not uploaded
+    // again.
     const long long N1 = (long long)n + 1;
     long long singles = 0, maxd = 0;
+    unsigned long long key = 0xcbf29ce484222325ull ^ (unsigned long long)n;
     for (long long k = 0; k < N1 * N1; ++k) {
         if (dist[k] < 0) return fail(ctx, CVRPSD_ERR_ARG, "negative distance");
         maxd = dist[k] > maxd ? dist[k] : maxd;
+        key = (key ^ (uint32_t)dist[k]) * 0x100000001b3ull;
     }
+    if (key == 0) key = 1;
     for (int c = 1; c <= n; ++c) singles += (long long)dist[c] + dist[(long long)c * N1];
     if (singles + (long long)n * maxd + 3 * maxd >= (1LL << 30))
         return fail(ctx, CVRPSD_ERR_OVERFLOW, "route costs of this instance could overflow int32");
@@ -102,12 +108,37 @@ int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, 
     if (!rc) rc = grow(ctx, &ctx->mt_acc, &acap, BACC_WORDS + 3LL * T, "accumulators");
     if (!rc) rc = grow(ctx, &ctx->mt_list, &ctx->mt_list_cap, std::min<long long>((long long)T * S, 1LL << 24),
                        "set-aside list");
-    if (!rc) rc = grow(ctx, &ctx->mt_dist, &ctx->mt_dist_cap, N1 * N1, "distances");
+    const bool same_dist = ctx->mt_dist && ctx->mt_dist_key == key && ctx->mt_dist_n == n;
+    if (!rc && !same_dist) {
+        ctx->mt_dist_key = 0;   // invalid until the new matrix is staged
+        rc = grow(ctx, &ctx->mt_dist, &ctx->mt_dist_cap, N1 * N1, "distances");
+        if (!rc && ctx->mt_dist_host_cap < N1 * N1) {
+            if (ctx->mt_dist_host) cudaFreeHost(ctx->mt_dist_host);
+            ctx->mt_dist_host = nullptr;
+            ctx->mt_dist_host_cap = 0;
+            if (host_alloc(ctx, &ctx->mt_dist_host, sizeof(int32_t) * N1 * N1) != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(ctx, CVRPSD_ERR_NOMEM, "pinned distances");
+            } else {
+                ctx->mt_dist_host_cap = N1 * N1;
+            }
+        }
+    }
     ctx->mt_descs_cap = (int)dcap;
     ctx->mt_acc_cap = (int)acap;
     if (rc) return rc;
-    CK(cudaMemcpyAsync(ctx->mt_dist, dist, sizeof(int32_t) * N1 * N1, cudaMemcpyHostToDevice, stream),
-       "upload distances");
+    if (!same_dist) {
+        if (!ctx->ev_dist) CK(cudaEventCreateWithFlags(&ctx->ev_dist, cudaEventDisableTiming), "cudaEventCreate");
+        // The pinned copy may still feed the previous upload (on any stream).
+        CK(cudaEventSynchronize(ctx->ev_dist), "cudaEventSynchronize");
+        memcpy(ctx->mt_dist_host, dist, sizeof(int32_t) * N1 * N1);
+        CK(cudaMemcpyAsync(ctx->mt_dist, ctx->mt_dist_host, sizeof(int32_t) * N1 * N1, cudaMemcpyHostToDevice,
+                           stream),
+           "upload distances");
+        CK(cudaEventRecord(ctx->ev_dist, stream), "cudaEventRecord");
+        ctx->mt_dist_key = key;
+        ctx->mt_dist_n = n;
+    }
     CK(cudaMemsetAsync(ctx->mt_acc, 0, sizeof(unsigned long long) * (BACC_WORDS + 3LL * T), stream),
        "clear accumulators");
     CK(launch_tour_tables(d_tours, T, n, ctx->mt_dist, nullptr, ctx->mt_tabs, ctx->mt_descs, demand, ld, Q,

@@ -81,11 +81,20 @@ class LocalSearch:
 
     def __init__(self, ctx, inst, D, start, *, surrogate: Surrogate | None = None, M: int = 4096, k: int = 64,
                  seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4,
-                 moves_block: int = 64):
+                 moves_block: int = 64, exact_all: bool = False):
+        """Three modes: with a surrogate, screen M neighbours and split the k
+        best exactly; with exact_all, split all M neighbours exactly (the
+        plain-Split search the screened one is measured against: same moves
+        for the same seed); otherwise split k random neighbours."""
         import torch
         self.ctx, self.inst, self.D = ctx, inst, D
         self.n = inst.n
-        self.M, self.k = (M if surrogate is not None else k), k
+        if surrogate is not None and exact_all:
+            raise ValueError("exact_all splits every neighbour: no surrogate")
+        self.exact_all = exact_all
+        self.M = M if (surrogate is not None or exact_all) else k
+        k = self.M if exact_all else k
+        self.k = k
         self.sur = surrogate
         self.rng = np.random.default_rng(seed)
         self.eval = Evaluator(ctx, inst, D)
@@ -134,6 +143,8 @@ class LocalSearch:
             cvrpsd_topk(self.ctx, self.scores, self.k, self.idx)
             cvrpsd_gather_tours(self.ctx, self.cand, self.idx, self.top)
             chosen = self.top
+        elif self.exact_all:
+            chosen = self.cand
         else:
             chosen = self.cand[: self.k]
         costs = self.eval(chosen)
@@ -155,18 +166,86 @@ class LocalSearch:
                     self.sur.train_step(tours, target, self.lr)
                 self.new_tours, self.new_costs = [], []
 
-    def run(self, iterations: int) -> SearchLog:
+    def run(self, iterations: int, seconds: float | None = None) -> SearchLog:
+        """`iterations` steps, or with `seconds` as many as fit in that wall
+        time (at most `iterations`; the clock is checked every 32 steps)."""
         import torch
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(iterations):
+        for it in range(iterations):
             self.step()
+            if seconds is not None and it % 32 == 31:
+                torch.cuda.synchronize()
+                if time.perf_counter() - t0 >= seconds:
+                    break
         torch.cuda.synchronize()
         self.log.seconds += time.perf_counter() - t0
+        self.flush()
+        return self.log
+
+    def flush(self):
+        """Move the device-side cost trace of the steps taken so far into
+        log.costs (step() alone only appends to the device trace)."""
+        import torch
         if self._trace:
             self.log.costs.extend(torch.cat(self._trace).tolist())
             self._trace = []
-        return self.log
+
+    @property
+    def iterations(self) -> int:
+        return self.log.screened // self.M
+
+
+def _ranks(x: np.ndarray) -> np.ndarray:
+    """Average ranks (ties share their mean rank), 0-based."""
+    order = np.argsort(x, kind="stable")
+    r = np.empty(len(x), dtype=np.float64)
+    r[order] = np.arange(len(x), dtype=np.float64)
+    xs = x[order]
+    i = 0
+    while i < len(x):
+        j = i
+        while j + 1 < len(x) and xs[j + 1] == xs[i]:
+            j += 1
+        if j > i:
+            r[order[i:j + 1]] = (i + j) / 2.0
+        i = j + 1
+    return r
+
+
+def spearman(a, b) -> float:
+    """Spearman rank correlation of two equally long sequences."""
+    ra, rb = _ranks(np.asarray(a, dtype=np.float64)), _ranks(np.asarray(b, dtype=np.float64))
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = float(np.sqrt((ra * ra).sum() * (rb * rb).sum()))
+    return float((ra * rb).sum() / den) if den > 0 else float("nan")
+
+
+def neighbourhood_quality(ctx, inst, D, sur: Surrogate, scale, tour, *, M: int = 4096, k: int = 64,
+                          seed: int = 0) -> dict:
+    """How well the surrogate ranks the M neighbours of one tour (what the
+    screen decides): exact SAA costs of all M by the GPU Split, surrogate
+    predictions in cost units, and their mean absolute error, Spearman rank
+    correlation, the share of the exact top-k among the surrogate's top-k,
+    and whether the exact best is in the surrogate's top-k."""
+    import torch
+    dev = D.device
+    rng = np.random.default_rng(seed)
+    moves = torch.from_numpy(random_moves(rng, M, inst.n)).to(dev)
+    base = torch.as_tensor(np.asarray(tour, dtype=np.int32), device=dev)
+    cand = torch.empty((M, inst.n), dtype=torch.int32, device=dev)
+    cvrpsd_neighbors(ctx, base, moves, cand)
+    exact = Evaluator(ctx, inst, D)(cand).cpu().numpy().astype(np.float64)
+    pred_t = torch.empty(M, dtype=torch.float32, device=dev)
+    sur.predict(cand, pred_t)
+    pred = pred_t.cpu().numpy().astype(np.float64) * scale[1] + scale[0]
+    top_pred = set(np.argsort(pred, kind="stable")[:k].tolist())
+    top_exact = np.argsort(exact, kind="stable")[:k].tolist()
+    return {"mae": float(np.abs(pred - exact).mean()), "spearman": spearman(pred, exact),
+            "recall_at_k": len(top_pred.intersection(top_exact)) / k,
+            "best_in_top_k": bool(int(np.argmin(exact)) in top_pred),
+            "exact_spread": float(exact.std()), "k": k, "M": M}
 
 
 def training_set(ctx, inst, D, count: int, seed: int = 0, chain: int = 64, chunk: int = 4096):

@@ -255,3 +255,72 @@ def test_more_training_scenarios_generalise_better(sp, cv):
     rows = search.oos_study(sp.ctx, inst, D_train, D_test, [1, 1000], iterations=150, seed=2)
     (s1, in1, out1), (s2, in2, out2) = rows
     assert out2 < out1
+
+
+def test_local_search_matches_host_accept_rule(sp, cv):
+    """The device-side choice and acceptance of LocalSearch against a host
+    replica: same seeded moves, neighbours built on the host from the moves'
+    definition, exact costs from the oracle, the best neighbour accepted only
+    if strictly cheaper. Same final tour, same cost trace (non-increasing),
+    and the reported cost is the exact cost of the final tour."""
+    from paper_2511_18022_gb300 import search
+    inst = make_instance(60, 1, 10, seed=13, Q=40, L=15)
+    S = 257
+    D = demand_matrix(inst.mu, inst.region, 1, 5, S, dtype=np.int16)
+    dD = torch.from_numpy(D).cuda()
+    start = np.random.default_rng(2).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    k, iters = 16, 100
+    ls = search.LocalSearch(sp.ctx, inst, dD, start, k=k, seed=77, moves_block=8)
+    for _ in range(iters):
+        ls.step()
+    ls.flush()
+
+    def cost(t):
+        _, s, inf, _ = oracle.split_costs(np.asarray(t, np.int32), inst.dist, D, inst.Q, inst.L)
+        return s / (S - inf)
+
+    rng = np.random.default_rng(77)
+    cur, cur_c, trace = list(start), cost(start), []
+    block = []
+    for _ in range(iters):
+        if not block:
+            block = [search.random_moves(rng, k, inst.n) for _ in range(8)]
+        moves = block.pop(0)
+        cands = [apply_move(cur, *(int(x) for x in m)) for m in moves]
+        cs = [cost(c) for c in cands]
+        b = int(np.argmin(cs))
+        if cs[b] < cur_c:
+            cur, cur_c = cands[b], cs[b]
+        trace.append(cur_c)
+    assert ls.cur.cpu().tolist() == cur
+    assert ls.log.costs == trace
+    assert all(b <= a for a, b in zip(trace, trace[1:]))
+    assert ls.cur_cost == cost(ls.cur.cpu().numpy())
+
+
+def test_screened_search_against_plain_split_search(sp, cv):
+    """The surrogate-screened search (screen M neighbours, split the k best)
+    against the plain-Split search that splits all M neighbours exactly, same
+    moves and start, reduced scale: at least 10x the candidate tours per
+    second, and within the same wall time a final SAA cost within 0.5 % of
+    the plain search's."""
+    from paper_2511_18022_gb300 import search
+    w = workload("surrogate-n200", S=8192)
+    inst = w.instances[0]
+    D = torch.empty((inst.n, w.S), dtype=torch.int16, device="cuda")
+    sp.gen_demand(w.scen_seeds[0], cv.GEN_CORRELATED, inst.mu, inst.region, D)
+    cust = search.customer_features(inst, D[:, :4096].cpu().numpy())
+    tours, costs = search.training_set(sp.ctx, inst, D, 40_000, seed=1)
+    sur = cv.Surrogate(sp.ctx, cust, inst.dist, Q=float(inst.Q), seed=7)
+    scale, _ = search.train_surrogate(sur, tours, costs, dist=inst.dist, epochs=8)
+    start = np.random.default_rng(5).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    plain = search.LocalSearch(sp.ctx, inst, D, start, M=2048, seed=9, exact_all=True)
+    plain.run(60)
+    screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=2048, k=32, seed=9, retrain_every=25,
+                                  scale=scale)
+    screened.run(100_000, seconds=plain.log.seconds)
+    assert screened.log.candidates_per_s >= 10 * plain.log.candidates_per_s
+    assert screened.cur_cost <= 1.005 * plain.cur_cost
+    q = search.neighbourhood_quality(sp.ctx, inst, D, sur, scale, screened.cur.cpu().numpy(), M=2048, k=32)
+    assert q["spearman"] > 0.3
+    sur.close()
