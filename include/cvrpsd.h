@@ -139,6 +139,18 @@ int cvrpsd_last_stats(const cvrpsd_ctx *ctx, cvrpsd_stats *stats);
  * durations in cvrpsd_stats. Off by default. */
 int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on);
 
+/* Messages of a context go to a caller-supplied function and nowhere else
+ * (the library never prints). Levels: */
+#define CVRPSD_LOG_ERROR 0   /* the detail of every failing call (also cvrpsd_last_error) */
+#define CVRPSD_LOG_INFO  1   /* tuning results, batch set-up */
+#define CVRPSD_LOG_DEBUG 2   /* per call: the kernel, walk and launch shape a Split ran */
+typedef void (*cvrpsd_log_fn)(int32_t level, const char *message, void *user);
+
+/* Route messages of level <= max_level to fn(level, message, user), called
+ * on the thread that makes the library call; fn = NULL turns logging off
+ * (the default). The message is valid only during the call. */
+int cvrpsd_set_log(cvrpsd_ctx *ctx, cvrpsd_log_fn fn, void *user, int32_t max_level);
+
 /* Input errors of calls that did not wait. A Split call that requests no
  * host output returns once its work is enqueued, before the kernels have
  * looked at the demands; a negative demand found there (that scenario's
@@ -320,13 +332,18 @@ int cvrpsd_batch_destroy(cvrpsd_batch *batch);
 
 /*
  * Autotuner of the batched path: for every launch shape of the persistent
- * batch kernel (threads {128, 256} x (spt 1, ring {16, 32}) or (spt 2, ring
- * 16)) create this batch, time its graph with CUDA events on `stream` (best
- * of three runs after one warm-up), and check that every tour's sum and
- * infeasible count equal those of the first shape (CVRPSD_ERR_DEVICE_STATUS
- * otherwise). The fastest shape becomes the context's configuration, so the
- * next cvrpsd_batch_create uses it; result->best_dtype is the batch's own
- * demand type. Arguments as for cvrpsd_batch_create. Synchronous.
+ * batch kernel -- scenarios per block 32 to 512 (threads {32, 64, 128, 256}
+ * x scenarios per thread {1, 2}) x deque ring (window tile) {16, 32, 64},
+ * 20 shapes (rings of 64 up to 128 threads) -- create this batch, time its
+ * graph with CUDA events on `stream` (best of three runs after one warm-up),
+ * and check that every tour's sum and infeasible count equal those of the
+ * first shape (CVRPSD_ERR_DEVICE_STATUS otherwise). The fastest shape becomes
+ * the context's configuration, so the next cvrpsd_batch_create uses it. Then
+ * the demand storage: the best shape runs on int16 and int32 copies of a
+ * sample of every tour's scenarios (at most 8192 columns and 2 GB of
+ * copies), both must give the same results, and result->best_dtype names the
+ * faster (int16 only if every demand fits). Arguments as for
+ * cvrpsd_batch_create. Synchronous; allocates the sample copies.
  */
 int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
                           int32_t demand_dtype, cvrpsd_tune_result *result, void *stream);

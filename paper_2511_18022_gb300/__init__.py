@@ -20,7 +20,7 @@ from ._lib import (CvrpsdError, Config, Stats, OK, WARN_INFEASIBLE, I16, I32, MA
 
 __all__ = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_set_config", "cvrpsd_get_config",
-    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_int_rate", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
+    "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_int_rate", "cvrpsd_set_log", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_autotune", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
@@ -93,6 +93,22 @@ def cvrpsd_set_profiling(ctx, on: bool) -> None:
 def cvrpsd_debug_fail_alloc(ctx, after: int) -> None:
     """Test hook: make the (after+1)-th next allocation of the context fail."""
     _lib.check(ctx, _lib.load().cvrpsd_debug_fail_alloc(ctx, int(after)))
+
+
+_log_keep = {}
+
+
+def cvrpsd_set_log(ctx, fn, max_level: int = 1) -> None:
+    """Send the context's messages of level <= max_level to fn(level, text)
+    (fn=None: off). The binding keeps the C callback alive with the context."""
+    key = ctx.value if isinstance(ctx, ctypes.c_void_p) else int(ctx)
+    if fn is None:
+        _lib.check(ctx, _lib.load().cvrpsd_set_log(ctx, _lib.LOG_FN(), None, -1))
+        _log_keep.pop(key, None)
+        return
+    cb = _lib.LOG_FN(lambda level, msg, user: fn(int(level), msg.decode(errors="replace")))
+    _log_keep[key] = cb
+    _lib.check(ctx, _lib.load().cvrpsd_set_log(ctx, cb, None, int(max_level)))
 
 
 def cvrpsd_check_inputs(ctx, stream=None) -> None:
@@ -572,6 +588,7 @@ class Splitter:
     def close(self):
         if self.ctx is not None:
             cvrpsd_destroy(self.ctx)
+            _log_keep.pop(self.ctx.value, None)
             self.ctx = None
 
     def __del__(self):
@@ -591,6 +608,9 @@ class Splitter:
 
     def check_inputs(self, stream=None):
         cvrpsd_check_inputs(self.ctx, stream)
+
+    def set_log(self, fn, max_level: int = 1):
+        cvrpsd_set_log(self.ctx, fn, max_level)
 
     def split(self, tour, dist, demand, Q, L=None, **kw) -> SplitResult:
         return cvrpsd_split_eval(self.ctx, tour, dist, demand, Q, L, **kw)

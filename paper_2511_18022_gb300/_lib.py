@@ -31,7 +31,7 @@ EXPORTS = [
     "cvrpsd_create", "cvrpsd_destroy", "cvrpsd_strerror", "cvrpsd_last_error",
     "cvrpsd_version", "cvrpsd_set_config", "cvrpsd_get_config", "cvrpsd_last_stats",
     "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_gen_demand", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc",
-    "cvrpsd_check_inputs", "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
+    "cvrpsd_check_inputs", "cvrpsd_set_log", "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
     "cvrpsd_batch_destroy", "cvrpsd_batch_autotune", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
     "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
     "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
@@ -40,6 +40,11 @@ EXPORTS = [
 ]
 SURROGATE_PARAMS = 67841
 NOALLOC_MAX_S = 1048576
+
+
+# void (*)(int32_t level, const char *message, void *user)
+LOG_FN = ctypes.CFUNCTYPE(None, ctypes.c_int32, ctypes.c_char_p, ctypes.c_void_p)
+LOG_ERROR, LOG_INFO, LOG_DEBUG = 0, 1, 2
 
 
 class Config(ctypes.Structure):
@@ -99,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_set_profiling.argtypes = [vp, i32]
     lib.cvrpsd_debug_fail_alloc.argtypes = [vp, ctypes.c_int32]
     lib.cvrpsd_check_inputs.argtypes = [vp, vp]
+    lib.cvrpsd_set_log.argtypes = [vp, LOG_FN, vp, i32]
     lib.cvrpsd_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.cvrpsd_split_eval.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_split_eval_host.argtypes = [vp, vp, i32, vp, vp, i32, i64, i64, i32, i32, vp, vp, vp, vp, vp]

@@ -25,6 +25,8 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("split_deque2.cu", [f"-DCVRPSD_DEQUE2_PART={k}"], f"split_deque2_{k}.o") for k in range(4)] + [
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=0"], "split_batch_0.o"),
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=1"], "split_batch_1.o"),
+    ("split_batch.cu", ["-DCVRPSD_BATCH_PART=2"], "split_batch_2.o"),
+    ("split_batch.cu", ["-DCVRPSD_BATCH_PART=3"], "split_batch_3.o"),
     ("split_warp.cu", [], "split_warp.o"),
     ("gen_demand.cu", [], "gen_demand.o"),
     ("api.cu", [], "api.o"),
@@ -97,6 +99,15 @@ def _build_locked(lib, bdir, jobs, extra_flags) -> str:
     return lib
 
 
+def build_checked(force: bool = False) -> str:
+    """The checked variant of the library (-DCVRPSD_CHECKED=1: every index a
+    Split kernel forms from data is compared with its buffer, and a bad one
+    is reported as CVRPSD_ERR_DEVICE_STATUS instead of being used) in its own
+    build folder; returns its path. A debugging aid, slower than the regular
+    build."""
+    return build(force=force, build_dir=BUILD + "-checked", extra_flags=["-DCVRPSD_CHECKED=1"])
+
+
 def resource_usage() -> str:
     """ptxas register / spill / shared-memory report of the last build."""
     out = []
@@ -108,4 +119,5 @@ def resource_usage() -> str:
 
 
 if __name__ == "__main__":
-    print(build(force=True))
+    import sys
+    print(build_checked(force=True) if "--checked" in sys.argv else build(force=True))

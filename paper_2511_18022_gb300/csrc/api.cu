@@ -16,6 +16,7 @@
 #include "ctx.h"
 #include "deque2.h"
 #include "kernels.h"
+#include "trace.h"
 #include "tour_table.h"
 
 using namespace cvrpsd;
@@ -173,6 +174,7 @@ const char *cvrpsd_last_error(const cvrpsd_ctx *ctx) { return ctx ? ctx->err : "
 
 int cvrpsd_create(cvrpsd_ctx **out, int device)
 {
+    CVRPSD_TRACE("cvrpsd_create");
     if (!out) return CVRPSD_ERR_ARG;
     *out = nullptr;
     int count = 0;
@@ -197,6 +199,7 @@ int cvrpsd_create(cvrpsd_ctx **out, int device)
 
 int cvrpsd_destroy(cvrpsd_ctx *ctx)
 {
+    CVRPSD_TRACE("cvrpsd_destroy");
     if (!ctx) return CVRPSD_ERR_ARG;
     cudaSetDevice(ctx->device);
     if (ctx->d_acc) cudaFree(ctx->d_acc);
@@ -272,8 +275,18 @@ int cvrpsd_set_profiling(cvrpsd_ctx *ctx, int32_t on)
     return CVRPSD_OK;
 }
 
+int cvrpsd_set_log(cvrpsd_ctx *ctx, cvrpsd_log_fn fn, void *user, int32_t max_level)
+{
+    if (!ctx) return CVRPSD_ERR_ARG;
+    ctx->log_fn = fn;
+    ctx->log_user = user;
+    ctx->log_level = fn ? max_level : -1;
+    return CVRPSD_OK;
+}
+
 int cvrpsd_check_inputs(cvrpsd_ctx *ctx, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_check_inputs");
     if (!ctx) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
     if (!ctx->d_acc || !ctx->h_acc) return CVRPSD_OK;   // no Split has run on this context
@@ -511,6 +524,8 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
     }
 launched:
     ctx->stats = st;
+    log_msg(ctx, CVRPSD_LOG_DEBUG, "split n=%d S=%lld: kernel %d walk %d threads %d spt %d ring %d rounds %d", n,
+            (long long)S, st.kernel, st.variant, st.threads, st.spt, st.ring, st.rounds);
     if (!out_sum && !out_infeasible && !out_mean && !host_buffers) return CVRPSD_OK;
 
     CK(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, ACC_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -528,6 +543,8 @@ launched:
             ctx->stats.fallback_ms = ms;
         }
     }
+    if (a[ACC_STATUS] & ST_INDEX)
+        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "a kernel index check failed (checked build)");
     if (a[ACC_STATUS] & ST_NEGATIVE_DEMAND)
         return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "negative demand found in the scenario matrix");
     const long long sum = (long long)a[ACC_SUM];
@@ -546,6 +563,7 @@ int cvrpsd_split_eval(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int
                       int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L, int32_t *out_cost,
                       int64_t *out_sum, int64_t *out_infeasible, double *out_mean, void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_split_eval");
     return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
                            out_mean, stream, nullptr, 0);
 }
@@ -555,6 +573,7 @@ int cvrpsd_split_eval_host(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, cons
                            int32_t *out_cost, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
                            void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_split_eval_host");
     if (!ctx) return CVRPSD_ERR_ARG;
     return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
                            out_mean, stream, nullptr, 0, true);
@@ -565,6 +584,7 @@ int cvrpsd_split_routes(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const i
                         int16_t *pred, int64_t ldp, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
                         void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_split_routes");
     if (!ctx) return CVRPSD_ERR_ARG;
     if (!pred) return fail(ctx, CVRPSD_ERR_ARG, "pred is required");
     return split_eval_impl(ctx, tour, n, dist, demand, demand_dtype, S, ld, Q, L, out_cost, out_sum, out_infeasible,
@@ -635,6 +655,7 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
                                const void *demand, int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L,
                                const char *cache_path, cvrpsd_tune_result *result, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_autotune");
     if (!ctx || !result) return CVRPSD_ERR_ARG;
     if (S < 1) return fail(ctx, CVRPSD_ERR_ARG, "autotune needs S >= 1");
     const cvrpsd_config saved = ctx->cfg;
@@ -752,6 +773,9 @@ extern "C" int cvrpsd_autotune(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, 
 
     ctx->cfg = best.best;
     ctx->profiling = saved_prof;
+    log_msg(ctx, CVRPSD_LOG_INFO, "autotune n=%d S=%lld: %d shapes, best walk %d threads %d spt %d ring %d "
+            "(%.4f ms), demand type %s", n, (long long)S, best.shapes_timed, best.best.variant, best.best.threads,
+            best.best.spt, best.best.ring, best.best_ms, best.best_dtype == CVRPSD_I16 ? "int16" : "int32");
     if (cache_path) {
         if (FILE *f = fopen(cache_path, "a")) {
             fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"spt\": %d, \"ring\": %d, \"variant\": %d, "
@@ -802,11 +826,7 @@ void batch_free(cvrpsd_batch *b)
     delete b;
 }
 
-bool valid_batch_shape(const DequeShape &s)
-{
-    return (s.threads == 128 || s.threads == 256) &&
-           ((s.spt == 1 && (s.ring == 16 || s.ring == 32)) || (s.spt == 2 && s.ring == 16));
-}
+bool valid_batch_shape(const DequeShape &s) { return batch_shape_compiled(s); }
 
 }  // namespace
 
@@ -815,6 +835,7 @@ extern "C" {
 int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S, int32_t demand_dtype,
                         cvrpsd_batch **out)
 {
+    CVRPSD_TRACE("cvrpsd_batch_create");
     if (!ctx || !out) return CVRPSD_ERR_ARG;
     *out = nullptr;
     ctx->err[0] = 0;
@@ -955,6 +976,7 @@ int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tour
 
 int cvrpsd_batch_run(cvrpsd_batch *b, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_batch_run");
     if (!b) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = b->ctx;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
@@ -968,11 +990,14 @@ int cvrpsd_batch_run(cvrpsd_batch *b, void *stream_ptr)
 int cvrpsd_batch_results(cvrpsd_batch *b, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
                          int32_t *out_status)
 {
+    CVRPSD_TRACE("cvrpsd_batch_results");
     if (!b) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = b->ctx;
     if (!b->ran) return fail(ctx, CVRPSD_ERR_ARG, "batch has not been run");
     CK(cudaEventSynchronize(b->done), "cudaEventSynchronize");
     const unsigned long long *h = b->h_acc;
+    if (h[BACC_STATUS] & ST_INDEX)
+        return fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "a kernel index check failed (checked build)");
     if (h[BACC_STATUS] & BST_LIST_FULL)
         return fail(ctx, CVRPSD_ERR_UNSUPPORTED, "more than %lld set-aside scenarios", (long long)b->bp.list_cap);
     ctx->stats.overflow = (int64_t)h[BACC_LIST];
@@ -1002,12 +1027,48 @@ int cvrpsd_batch_destroy(cvrpsd_batch *b)
     return CVRPSD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device time of one graph run of a batch in shape `cfg` (best of three after
+// a warm-up), with the per-tour sums and infeasible counts of the last run.
+int time_batch(cvrpsd_ctx *ctx, const cvrpsd_config &cfg, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
+               int32_t dtype, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t stream, float *ms_out,
+               std::vector<int64_t> &sum, std::vector<int64_t> &inf, cvrpsd_config *ran)
+{
+    ctx->cfg = cfg;
+    cvrpsd_batch *b = nullptr;
+    int rc = cvrpsd_batch_create(ctx, T, tours, S, dtype, &b);
+    if (rc) return rc;
+    // the shape the batch actually runs (it may shrink to fit)
+    *ran = cvrpsd_config{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring, 0, 0};
+    float t_best = 1e30f;
+    for (int rep = 0; rep < 4 && rc >= 0; ++rep) {
+        cudaEventRecord(ev0, stream);
+        rc = cvrpsd_batch_run(b, stream);
+        cudaEventRecord(ev1, stream);
+        if (rc >= 0) rc = cvrpsd_batch_results(b, sum.data(), inf.data(), nullptr, nullptr);
+        float ms = 0;
+        if (rc >= 0 && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess && rep > 0 && ms < t_best)
+            t_best = ms;   // the first run warms up
+    }
+    cvrpsd_batch_destroy(b);
+    *ms_out = t_best;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
 int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tours, int64_t S,
                           int32_t demand_dtype, cvrpsd_tune_result *result, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_batch_autotune");
     if (!ctx || !result) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
-    if (T < 1) return fail(ctx, CVRPSD_ERR_ARG, "T = %d", T);
+    if (T < 1 || !tours) return fail(ctx, CVRPSD_ERR_ARG, "T = %d", T);
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
     const cvrpsd_config saved = ctx->cfg;
     std::vector<int64_t> ref_sum((size_t)T), ref_inf((size_t)T), sum((size_t)T), inf((size_t)T);
@@ -1023,42 +1084,82 @@ int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *to
     best.best_dtype = demand_dtype;
     int rc = CVRPSD_OK;
     bool have_ref = false;
-    static const DequeShape kShapes[] = {{128, 1, 16}, {128, 1, 32}, {128, 2, 16},
-                                         {256, 1, 16}, {256, 1, 32}, {256, 2, 16}};
-    for (const DequeShape &sh : kShapes) {
-        ctx->cfg = cvrpsd_config{CVRPSD_KERNEL_DEQUE, sh.threads, sh.spt, sh.ring};
-        cvrpsd_batch *b = nullptr;
-        rc = cvrpsd_batch_create(ctx, T, tours, S, demand_dtype, &b);
-        if (rc) break;
-        // the shape the batch actually runs (it may shrink to fit)
-        const cvrpsd_config ran{CVRPSD_KERNEL_DEQUE, ctx->stats.threads, ctx->stats.spt, ctx->stats.ring};
-        float t_best = 1e30f;
-        for (int rep = 0; rep < 4 && rc >= 0; ++rep) {
-            cudaEventRecord(ev[0], stream);
-            rc = cvrpsd_batch_run(b, stream);
-            cudaEventRecord(ev[1], stream);
-            if (rc >= 0) rc = cvrpsd_batch_results(b, sum.data(), inf.data(), nullptr, nullptr);
-            float ms = 0;
-            if (rc >= 0 && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && rep > 0 && ms < t_best)
-                t_best = ms;   // the first run warms up
+    // Scenarios per block 32..512 (threads x scenarios per thread) x deque
+    // ring 16 / 32 / 64 (the window tile), every shape the kernel is compiled for.
+    for (int threads : {32, 64, 128, 256})
+        for (int spt : {1, 2})
+            for (int ring : {16, 32, 64}) {
+                if (rc < 0 || !batch_shape_compiled(DequeShape{threads, spt, ring})) continue;
+                const cvrpsd_config cfg{CVRPSD_KERNEL_DEQUE, threads, spt, ring, 0, 0};
+                cvrpsd_config ran{};
+                float t = 0;
+                rc = time_batch(ctx, cfg, T, tours, S, demand_dtype, ev[0], ev[1], stream, &t, sum, inf, &ran);
+                if (rc < 0) break;
+                if (!have_ref) {
+                    ref_sum = sum;
+                    ref_inf = inf;
+                    have_ref = true;
+                } else if (sum != ref_sum || inf != ref_inf) {
+                    rc = fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "batch shape %d/%d/%d changes a tour's result", threads,
+                              spt, ring);
+                    break;
+                }
+                ++best.shapes_timed;
+                if (t < best.best_ms) {
+                    best.best_ms = t;
+                    best.best = ran;
+                }
+            }
+    // Demand storage: the best shape on int16 and int32 copies of a sample of
+    // every tour's scenarios (at most 2 GB of copies), bit-checked against
+    // each other; int16 only if every demand fits.
+    const long long total_n = [&] {
+        long long t = 0;
+        for (int k = 0; k < T; ++k) t += tours[k].n;
+        return t;
+    }();
+    long long Ss = std::min<long long>(S, 8192);
+    Ss = std::min<long long>(Ss, std::max<long long>(32, (2000000000LL / (6 * std::max<long long>(total_n, 1))) / 32 * 32));
+    void *tmp16 = nullptr, *tmp32 = nullptr;
+    unsigned int *sat = nullptr;
+    if (rc >= 0 && Ss >= 1 && dev_alloc(ctx, &tmp16, (size_t)total_n * Ss * 2) == cudaSuccess &&
+        dev_alloc(ctx, &tmp32, (size_t)total_n * Ss * 4) == cudaSuccess &&
+        dev_alloc(ctx, &sat, sizeof(unsigned int)) == cudaSuccess && cudaMemsetAsync(sat, 0, 4, stream) == cudaSuccess) {
+        std::vector<cvrpsd_tour_desc> d16(tours, tours + T), d32(tours, tours + T);
+        long long row = 0;
+        bool ok = true;
+        for (int k = 0; k < T && ok; ++k) {
+            char *p16 = static_cast<char *>(tmp16) + row * Ss * 2, *p32 = static_cast<char *>(tmp32) + row * Ss * 4;
+            ok = launch_convert_demand(tours[k].demand, demand_dtype, tours[k].ld, p16, 2, Ss, tours[k].n, Ss, sat,
+                                       stream) == cudaSuccess &&
+                 launch_convert_demand(tours[k].demand, demand_dtype, tours[k].ld, p32, 4, Ss, tours[k].n, Ss, sat,
+                                       stream) == cudaSuccess;
+            d16[k].demand = p16;
+            d32[k].demand = p32;
+            d16[k].ld = d32[k].ld = Ss;
+            d16[k].out_cost = d32[k].out_cost = nullptr;
+            row += tours[k].n;
         }
-        cvrpsd_batch_destroy(b);
-        if (rc < 0) break;
-        if (!have_ref) {
-            ref_sum = sum;
-            ref_inf = inf;
-            have_ref = true;
-        } else if (sum != ref_sum || inf != ref_inf) {
-            rc = fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "batch shape %d/%d/%d changes a tour's result", sh.threads,
-                      sh.spt, sh.ring);
-            break;
-        }
-        ++best.shapes_timed;
-        if (t_best < best.best_ms) {
-            best.best_ms = t_best;
-            best.best = ran;
+        unsigned int h_sat = 1;
+        if (ok && cudaMemcpyAsync(&h_sat, sat, 4, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+            cudaStreamSynchronize(stream) == cudaSuccess) {
+            std::vector<int64_t> s16((size_t)T), i16((size_t)T);
+            cvrpsd_config ran{};
+            float t16 = 1e30f, t32 = 1e30f;
+            const bool r32 = time_batch(ctx, best.best, T, d32.data(), Ss, CVRPSD_I32, ev[0], ev[1], stream, &t32,
+                                        sum, inf, &ran) >= 0;
+            const bool r16 = !h_sat && time_batch(ctx, best.best, T, d16.data(), Ss, CVRPSD_I16, ev[0], ev[1], stream,
+                                                  &t16, s16, i16, &ran) >= 0;
+            if (r16 && r32 && (s16 != sum || i16 != inf))
+                rc = fail(ctx, CVRPSD_ERR_DEVICE_STATUS, "int16 and int32 copies of the demands disagree");
+            else if (r32 || r16)
+                best.best_dtype = (r16 && t16 <= t32) ? CVRPSD_I16 : CVRPSD_I32;
         }
     }
+    cudaGetLastError();
+    if (tmp16) cudaFree(tmp16);
+    if (tmp32) cudaFree(tmp32);
+    if (sat) cudaFree(sat);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     if (rc < 0) {
@@ -1067,6 +1168,9 @@ int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *to
     }
     ctx->cfg = best.best;
     *result = best;
+    log_msg(ctx, CVRPSD_LOG_INFO, "batch autotune T=%d S=%lld: %d shapes, best threads %d spt %d ring %d "
+            "(%.4f ms), demand type %s", T, (long long)S, best.shapes_timed, best.best.threads, best.best.spt,
+            best.best.ring, best.best_ms, best.best_dtype == CVRPSD_I16 ? "int16" : "int32");
     return CVRPSD_OK;
 }
 
@@ -1074,6 +1178,7 @@ int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *
                             int32_t demand_dtype, int64_t *out_sum, int64_t *out_infeasible, double *out_mean,
                             int32_t *out_status, void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_split_eval_batch");
     cvrpsd_batch *b = nullptr;
     int rc = cvrpsd_batch_create(ctx, T, tours, S, demand_dtype, &b);
     if (rc) return rc;
@@ -1086,6 +1191,7 @@ int cvrpsd_split_eval_batch(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *
 int cvrpsd_gen_demand(cvrpsd_ctx *ctx, uint64_t seed, int32_t kind, const int32_t *mu, const int32_t *region,
                       int32_t n, int64_t S, int64_t ld, int32_t dtype, void *out, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_gen_demand");
     if (!ctx) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);

@@ -56,9 +56,25 @@ struct cvrpsd_ctx {
     long long seq_mats_cap = 0;
     // test hook (cvrpsd_debug_fail_alloc): allocations left before one fails; -1 = off
     int fail_alloc_after = -1;
+    // caller's log sink (cvrpsd_set_log)
+    cvrpsd_log_fn log_fn = nullptr;
+    void *log_user = nullptr;
+    int log_level = -1;
 };
 
 namespace cvrpsd {
+
+// A message to the context's log sink, if one takes this level.
+inline void log_msg(cvrpsd_ctx *ctx, int level, const char *fmt, ...)
+{
+    if (!ctx || !ctx->log_fn || level > ctx->log_level) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->log_fn(level, buf, ctx->log_user);
+}
 
 inline int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -67,6 +83,7 @@ inline int fail(cvrpsd_ctx *ctx, int code, const char *fmt, ...)
         va_start(ap, fmt);
         vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
         va_end(ap);
+        log_msg(ctx, CVRPSD_LOG_ERROR, "error %d: %s", code, ctx->err);
     }
     return code;
 }

@@ -13,8 +13,30 @@ namespace cvrpsd {
 enum AccWord { ACC_SUM = 0, ACC_INFEASIBLE = 1, ACC_OVERFLOW = 2, ACC_STATUS = 3, ACC_WORDS = 4, ACC_STICKY = 4,
                ACC_ALLOC_WORDS = 8 };
 
-// Device status bits (ACC_STATUS).
-enum StatusBits { ST_NEGATIVE_DEMAND = 1 };
+// Device status bits (ACC_STATUS, and a batch's BACC_STATUS).
+enum StatusBits { ST_NEGATIVE_DEMAND = 1, ST_INDEX = 2 };
+
+// Checked build (compile with -DCVRPSD_CHECKED=1): every index a Split kernel
+// forms from data (table rows, scenario columns, list entries) is compared
+// with its buffer before use; a bad one sets ST_INDEX in `status` and the
+// access is skipped. Nothing traps. The regular build compiles the checks
+// away.
+#ifndef CVRPSD_CHECKED
+#define CVRPSD_CHECKED 0
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ bool index_ok(bool ok, unsigned long long *status)
+{
+#if CVRPSD_CHECKED
+    if (!ok) atomicOr(status, (unsigned long long)ST_INDEX);
+    return ok;
+#else
+    (void)status;
+    (void)ok;
+    return true;
+#endif
+}
+#endif
 
 // One tour position as the kernels read it: the demand row of sigma_i and the
 // scenario-independent cost term C_i (see api.cu: C_i = c(sigma_i,0) +
@@ -85,7 +107,7 @@ struct TourDev {
 // Batch accumulator header; per tour three words follow: sum, infeasible
 // count, status bits.
 enum BatchAccWord { BACC_COUNTER = 0, BACC_LIST = 1, BACC_STATUS = 2, BACC_WORDS = 4 };
-enum BatchStatusBits { BST_LIST_FULL = 1 };
+enum BatchStatusBits { BST_LIST_FULL = 1 };   // shares its word with ST_INDEX (2)
 
 struct BatchParams {
     const TourDev *tours;         // device [T]
@@ -110,10 +132,16 @@ inline size_t split_batch_smem(int max_n, const DequeShape &shape)
 // reports blocks per SM in *blocks_per_sm.
 cudaError_t launch_split_batch(const BatchParams &b, int esize, bool lcap, const DequeShape &shape, int grid,
                                bool configure_only, int *blocks_per_sm, cudaStream_t stream);
-cudaError_t launch_split_batch_i16(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
-                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream);
-cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
-                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i16_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                       int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i16_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                         int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i32_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                       int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch_i32_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                         int *blocks_per_sm, cudaStream_t stream);
+// Whether the batch kernel is compiled for this (threads, spt, ring).
+bool batch_shape_compiled(const DequeShape &s);
 cudaError_t launch_split_warp_batch(const BatchParams &b, int esize, int grid_ctas, int max_smem, bool configure_only,
                                     cudaStream_t stream);
 

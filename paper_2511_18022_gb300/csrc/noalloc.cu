@@ -23,6 +23,7 @@
 
 #include "../../include/cvrpsd.h"
 #include "kernels.h"
+#include "trace.h"
 #include "tour_table.h"
 
 namespace {
@@ -100,6 +101,7 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
                                          int32_t *out_cost, int64_t *out_sum, int64_t *out_infeasible,
                                          double *out_mean, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_split_eval_noalloc");
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
     if (!tour || !dist || n < 1 || n > CVRPSD_MAX_N) return CVRPSD_ERR_ARG;
     if (demand_dtype != CVRPSD_I16 && demand_dtype != CVRPSD_I32) return CVRPSD_ERR_DTYPE;
@@ -197,7 +199,7 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
         cudaGetLastError();
         return CVRPSD_ERR_CUDA;
     }
-    if (h[ACC_STATUS] & ST_NEGATIVE_DEMAND) return CVRPSD_ERR_DEVICE_STATUS;
+    if (h[ACC_STATUS] & (ST_NEGATIVE_DEMAND | ST_INDEX)) return CVRPSD_ERR_DEVICE_STATUS;
     const long long sum = (long long)h[ACC_SUM], inf = (long long)h[ACC_INFEASIBLE];
     if (out_sum) *out_sum = sum;
     if (out_infeasible) *out_infeasible = inf;

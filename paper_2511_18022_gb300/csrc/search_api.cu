@@ -10,6 +10,7 @@
 
 #include "ctx.h"
 #include "kernels.h"
+#include "trace.h"
 #include "mlp.h"
 #include "tour_table.h"
 
@@ -61,6 +62,7 @@ int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, 
                             const void *demand, int32_t demand_dtype, int64_t S, int64_t ld, int32_t Q, int32_t L,
                             double *d_mean, int64_t *d_sum, int64_t *d_infeasible, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_split_eval_tours");
     if (!ctx) return CVRPSD_ERR_ARG;
     ctx->err[0] = 0;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
@@ -178,6 +180,7 @@ int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, 
 int cvrpsd_neighbors(cvrpsd_ctx *ctx, const int32_t *d_base, int32_t n, const int32_t *d_moves, int32_t M,
                      int32_t *d_out, void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_neighbors");
     if (!ctx) return CVRPSD_ERR_ARG;
     if (n < 1 || M < 0) return fail(ctx, CVRPSD_ERR_ARG, "n = %d, M = %d", n, M);
     if (M == 0) return CVRPSD_OK;
@@ -191,6 +194,7 @@ int cvrpsd_neighbors(cvrpsd_ctx *ctx, const int32_t *d_base, int32_t n, const in
 
 int cvrpsd_topk(cvrpsd_ctx *ctx, const float *d_scores, int32_t M, int32_t k, int32_t *d_idx, void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_topk");
     if (!ctx) return CVRPSD_ERR_ARG;
     if (M < 1 || M > 16384 || k < 1 || k > M) return fail(ctx, CVRPSD_ERR_ARG, "M = %d, k = %d", M, k);
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -203,6 +207,7 @@ int cvrpsd_topk(cvrpsd_ctx *ctx, const float *d_scores, int32_t M, int32_t k, in
 int cvrpsd_gather_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t rows, int32_t n, const int32_t *d_idx,
                         int32_t R, int32_t *d_out, void *stream)
 {
+    CVRPSD_TRACE("cvrpsd_gather_tours");
     if (!ctx) return CVRPSD_ERR_ARG;
     if (n < 1 || R < 0 || rows < 1) return fail(ctx, CVRPSD_ERR_ARG, "rows = %d, n = %d, R = %d", rows, n, R);
     if (R == 0) return CVRPSD_OK;
@@ -309,6 +314,7 @@ extern "C" {
 int cvrpsd_surrogate_create(cvrpsd_ctx *ctx, int32_t n, const float *cust, const int32_t *dist, float Q, uint64_t seed,
                             cvrpsd_surrogate **out)
 {
+    CVRPSD_TRACE("cvrpsd_surrogate_create");
     if (!ctx || !out) return CVRPSD_ERR_ARG;
     *out = nullptr;
     if (n < 1 || n > 4096 || !cust || !dist || !(Q > 0))
@@ -388,6 +394,7 @@ int cvrpsd_surrogate_destroy(cvrpsd_surrogate *s)
 
 int cvrpsd_surrogate_predict(cvrpsd_surrogate *s, const int32_t *d_tours, int32_t T, float *d_pred, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_surrogate_predict");
     if (!s) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = s->ctx;
     int rc = sur_check(s, d_tours, T);
@@ -414,6 +421,7 @@ static int sur_grad(cvrpsd_surrogate *s, const int32_t *d_tours, int32_t T, cons
 int cvrpsd_surrogate_train_step(cvrpsd_surrogate *s, const int32_t *d_tours, int32_t T, const float *d_target,
                                 float lr, float *d_loss, void *stream_ptr)
 {
+    CVRPSD_TRACE("cvrpsd_surrogate_train_step");
     if (!s) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = s->ctx;
     int rc = sur_check(s, d_tours, T);
@@ -431,6 +439,7 @@ int cvrpsd_surrogate_train_step(cvrpsd_surrogate *s, const int32_t *d_tours, int
 int cvrpsd_surrogate_gradients(cvrpsd_surrogate *s, const int32_t *d_tours, int32_t T, const float *d_target,
                                float *h_grad, float *h_loss)
 {
+    CVRPSD_TRACE("cvrpsd_surrogate_gradients");
     if (!s || !h_grad) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = s->ctx;
     int rc = sur_check(s, d_tours, T);
@@ -482,6 +491,7 @@ constexpr uint32_t kSurrogateStateMagic = 0x53504443u;
 
 int cvrpsd_surrogate_state(cvrpsd_surrogate *s, void *h_get, const void *h_set, int64_t *bytes)
 {
+    CVRPSD_TRACE("cvrpsd_surrogate_state");
     if (!s) return CVRPSD_ERR_ARG;
     cvrpsd_ctx *ctx = s->ctx;
     const size_t arr = sizeof(float) * (size_t)kMlpParams;

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
         const int item = s_item;
         if (item >= b.n_items) break;
         const int2 it = b.items ? b.items[item] : make_int2(item / b.tiles, item % b.tiles);
+        if (!index_ok(it.x >= 0 && it.y >= 0 && (long long)it.y * T * SPT < b.S, b.acc + BACC_STATUS)) continue;
         const TourDev td = b.tours[it.x];
         const int t = it.x;
         if (t != cur) {   // block-uniform; the loop-top barrier has retired the previous item
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(T) split_batch_kernel(BatchParams b)
                 const unsigned long long idx = atomicAdd(acc + BACC_LIST, 1ull);
                 if ((long long)idx < cap) list[idx] = make_int2(t, (int)s);
                 else atomicOr(acc + BACC_STATUS, (unsigned long long)BST_LIST_FULL);
-            });
+            },
+            b.acc + BACC_STATUS);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0) s_sum[w] = sum;
@@ -77,38 +79,69 @@ static cudaError_t launch_one(const BatchParams &b, const DequeShape &shape, int
     return cudaGetLastError();
 }
 
-template <typename DT>
-static cudaError_t dispatch(const BatchParams &b, bool lcap, const DequeShape &s, int grid, bool configure_only,
+// Launch shapes compiled for the batch kernel (threads, scenarios per
+// thread, ring): scenarios per block 32..256 (and 512) with rings of 16, 32
+// and 64 entries (64 only up to 128 threads: larger blocks of 64-entry rings
+// leave room for one block per SM).
+#define CVRPSD_BATCH_SHAPES(X)                                                                  \
+    X(32, 1, 16) X(32, 1, 32) X(32, 1, 64) X(32, 2, 16) X(32, 2, 32) X(32, 2, 64)               \
+    X(64, 1, 16) X(64, 1, 32) X(64, 1, 64) X(64, 2, 16) X(64, 2, 32) X(64, 2, 64)               \
+    X(128, 1, 16) X(128, 1, 32) X(128, 1, 64) X(128, 2, 16) X(128, 2, 32)                      \
+    X(256, 1, 16) X(256, 1, 32) X(256, 2, 16)
+
+template <typename DT, bool LCAP>
+static cudaError_t dispatch(const BatchParams &b, const DequeShape &s, int grid, bool configure_only,
                             int *blocks_per_sm, cudaStream_t st)
 {
-#define CVRPSD_CASE(T_, SPT_, R_)                                                                       \
-    if (s.threads == T_ && s.spt == SPT_ && s.ring == R_)                                              \
-        return lcap ? launch_one<DT, SPT_, R_, T_, true>(b, s, grid, configure_only, blocks_per_sm, st) \
-                    : launch_one<DT, SPT_, R_, T_, false>(b, s, grid, configure_only, blocks_per_sm, st);
-    CVRPSD_CASE(128, 1, 16) CVRPSD_CASE(128, 1, 32) CVRPSD_CASE(256, 1, 16) CVRPSD_CASE(256, 1, 32)
-    CVRPSD_CASE(128, 2, 16) CVRPSD_CASE(256, 2, 16)
+#define CVRPSD_CASE(T_, SPT_, R_)                                                      \
+    if (s.threads == T_ && s.spt == SPT_ && s.ring == R_)                             \
+        return launch_one<DT, SPT_, R_, T_, LCAP>(b, s, grid, configure_only, blocks_per_sm, st);
+    CVRPSD_BATCH_SHAPES(CVRPSD_CASE)
 #undef CVRPSD_CASE
     return cudaErrorInvalidValue;
 }
 
 #if CVRPSD_BATCH_PART == 0
-cudaError_t launch_split_batch_i16(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
-                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream)
+bool batch_shape_compiled(const DequeShape &s)
 {
-    return dispatch<int16_t>(b, lcap, shape, grid, configure_only, blocks_per_sm, stream);
+#define CVRPSD_CASE(T_, SPT_, R_) if (s.threads == T_ && s.spt == SPT_ && s.ring == R_) return true;
+    CVRPSD_BATCH_SHAPES(CVRPSD_CASE)
+#undef CVRPSD_CASE
+    return false;
+}
+
+cudaError_t launch_split_batch_i16_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                       int *blocks_per_sm, cudaStream_t stream)
+{
+    return dispatch<int16_t, true>(b, shape, grid, configure_only, blocks_per_sm, stream);
 }
 
 cudaError_t launch_split_batch(const BatchParams &b, int esize, bool lcap, const DequeShape &shape, int grid,
                                bool configure_only, int *blocks_per_sm, cudaStream_t stream)
 {
-    return esize == 2 ? launch_split_batch_i16(b, lcap, shape, grid, configure_only, blocks_per_sm, stream)
-                      : launch_split_batch_i32(b, lcap, shape, grid, configure_only, blocks_per_sm, stream);
+    if (esize == 2)
+        return lcap ? launch_split_batch_i16_cap(b, shape, grid, configure_only, blocks_per_sm, stream)
+                    : launch_split_batch_i16_nocap(b, shape, grid, configure_only, blocks_per_sm, stream);
+    return lcap ? launch_split_batch_i32_cap(b, shape, grid, configure_only, blocks_per_sm, stream)
+                : launch_split_batch_i32_nocap(b, shape, grid, configure_only, blocks_per_sm, stream);
+}
+#elif CVRPSD_BATCH_PART == 1
+cudaError_t launch_split_batch_i16_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                         int *blocks_per_sm, cudaStream_t stream)
+{
+    return dispatch<int16_t, false>(b, shape, grid, configure_only, blocks_per_sm, stream);
+}
+#elif CVRPSD_BATCH_PART == 2
+cudaError_t launch_split_batch_i32_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                       int *blocks_per_sm, cudaStream_t stream)
+{
+    return dispatch<int32_t, true>(b, shape, grid, configure_only, blocks_per_sm, stream);
 }
 #else
-cudaError_t launch_split_batch_i32(const BatchParams &b, bool lcap, const DequeShape &shape, int grid,
-                                   bool configure_only, int *blocks_per_sm, cudaStream_t stream)
+cudaError_t launch_split_batch_i32_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                         int *blocks_per_sm, cudaStream_t stream)
 {
-    return dispatch<int32_t>(b, lcap, shape, grid, configure_only, blocks_per_sm, stream);
+    return dispatch<int32_t, false>(b, shape, grid, configure_only, blocks_per_sm, stream);
 }
 #endif
 

@@ -278,12 +278,24 @@ __device__ __forceinline__ void walk_block(Deque (&d)[SPT], const uint32_t (&rin
 // n (in bounds, unused), which keeps the loads free of branches.
 template <typename DT, int SPT, bool CLAMP = true, typename TB>
 __device__ __forceinline__ void prefetch_block(const char *base, const TB &tab, int i0, int n, uint32_t ldb,
-                                               bool full, int nvalid, int (&q)[kPrefetch][SPT])
+                                               bool full, int nvalid, unsigned long long *status,
+                                               int (&q)[kPrefetch][SPT])
 {
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
         const int i = CLAMP ? min(i0 + u, n) : i0 + u;
-        load_demands<DT, SPT>(base, tab.row(i) & kRowMask, ldb, full, nvalid, q[u]);
+        if (!index_ok(i >= 1 && i <= n, status)) {
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) q[u][j] = 0;
+            continue;
+        }
+        const int row = tab.row(i) & kRowMask;
+        if (!index_ok(row < n, status)) {
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) q[u][j] = 0;
+            continue;
+        }
+        load_demands<DT, SPT>(base, row, ldb, full, nvalid, q[u]);
     }
 }
 
@@ -297,7 +309,8 @@ template <typename DT, int SPT, int R, int T, bool LCAP, typename SetAside, bool
 __device__ __forceinline__ long long split_thread(const void *demand, long long ld, long long S, long long s_first,
                                                   int n, int Q, int L, uint32_t K, int g0, uint32_t rings,
                                                   TB tab, int tid, int32_t *out_cost, SetAside set_aside,
-                                                  int16_t *pred_base = nullptr, long long ldp = 0)
+                                                  unsigned long long *status, int16_t *pred_base = nullptr,
+                                                  long long ldp = 0)
 {
     using RG = Ring<R, T>;
     const long long rem = S - s_first;
@@ -329,22 +342,22 @@ __device__ __forceinline__ long long split_thread(const void *demand, long long 
     }
 
     int qa[kPrefetch][SPT], qb[kPrefetch][SPT];
-    prefetch_block<DT, SPT>(base, tab, 1, n, ldb, full, nvalid, qa);
+    prefetch_block<DT, SPT>(base, tab, 1, n, ldb, full, nvalid, status, qa);
     int i0 = 1;
     // Double blocks whose positions, and those of the next prefetch, are all
     // below n: no guards or clamps.
     for (; i0 + 3 * kPrefetch - 1 < n; i0 += 2 * kPrefetch) {
-        prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+        prefetch_block<DT, SPT, false>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, status, qb);
         walk_block<DT, SPT, R, T, LCAP, false, PRED>(d, ring, qa, tab, i0, n, K, QK, L, Q, out, pred, ldp);
-        prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+        prefetch_block<DT, SPT, false>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, status, qa);
         walk_block<DT, SPT, R, T, LCAP, false, PRED>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out, pred, ldp);
     }
     // The remaining positions i0 .. n (qa holds i0 .. i0 + kPrefetch - 1).
     for (; i0 <= n; i0 += 2 * kPrefetch) {
-        prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, qb);
+        prefetch_block<DT, SPT>(base, tab, i0 + kPrefetch, n, ldb, full, nvalid, status, qb);
         walk_block<DT, SPT, R, T, LCAP, true, PRED>(d, ring, qa, tab, i0, n, K, QK, L, Q, out, pred, ldp);
         if (i0 + kPrefetch > n) break;
-        prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, qa);
+        prefetch_block<DT, SPT>(base, tab, i0 + 2 * kPrefetch, n, ldb, full, nvalid, status, qa);
         walk_block<DT, SPT, R, T, LCAP, true, PRED>(d, ring, qb, tab, i0 + kPrefetch, n, K, QK, L, Q, out, pred, ldp);
     }
 
@@ -385,13 +398,14 @@ __global__ void __launch_bounds__(T, d1_min_blocks<T>()) split_deque_kernel(Spli
     const long long s_first = ((long long)blockIdx.x * T + tid) * SPT;
     unsigned long long *acc = p.acc;
     int32_t *list = p.ovf_list;
-    auto set_aside = [acc, list](long long s) {
+    const long long S = p.S;
+    auto set_aside = [acc, list, S](long long s) {
         const unsigned long long idx = atomicAdd(acc + ACC_OVERFLOW, 1ull);
-        list[idx] = (int32_t)s;
+        if (index_ok(idx < (unsigned long long)S, acc + ACC_STATUS)) list[idx] = (int32_t)s;
     };
     const long long sum = split_thread<DT, SPT, R, T, LCAP, decltype(set_aside), PRED>(
-        p.demand, p.ld, p.S, s_first, n, p.Q, p.L, p.K, p.g0, sbase, tab, tid, p.out_cost, set_aside, p.pred,
-        p.ldp);
+        p.demand, p.ld, p.S, s_first, n, p.Q, p.L, p.K, p.g0, sbase, tab, tid, p.out_cost, set_aside,
+        p.acc + ACC_STATUS, p.pred, p.ldp);
     block_accumulate(sum, 0u, 0u, p.acc);
 }
 

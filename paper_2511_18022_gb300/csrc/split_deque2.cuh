@@ -143,9 +143,12 @@ template <> struct Dem2<int16_t> { using T = unsigned short; };
 template <> struct Dem2<int32_t> { using T = unsigned int; };
 
 template <typename DT, int CAP>
-__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i, uint32_t pitch)
+__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i, uint32_t pitch,
+                                              int n, unsigned long long *status)
 {
+    if (!index_ok(i >= 1 && i <= n && i <= CAP, status)) return 0u;
     const uint32_t row = tab.e[i - 1].x & kTab2RowMask;
+    if (!index_ok(row < (uint32_t)n, status)) return 0u;
     return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + (unsigned long long)row * pitch));
 }
 
@@ -183,10 +186,11 @@ __device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPref
 
 template <typename DT, bool CLAMPI, int CAP>
 __device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n, uint32_t pitch,
-                                          uint32_t (&q)[kPrefetch2])
+                                          unsigned long long *status, uint32_t (&q)[kPrefetch2])
 {
 #pragma unroll
-    for (int u = 0; u < kPrefetch2; ++u) q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u, pitch);
+    for (int u = 0; u < kPrefetch2; ++u)
+        q[u] = load_dem2<DT>(base, tab, CLAMPI ? min(i0 + u, n) : i0 + u, pitch, n, status);
 }
 
 // The walk of one scenario (column s; a thread past S walks column 0 and
@@ -212,19 +216,20 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     int out = 0;
     uint32_t qa[kPrefetch2], qb[kPrefetch2];
     const uint32_t pitch = p.pitch;
-    prefetch2<DT, true>(base, tab, 1, n, pitch, qa);
+    unsigned long long *status = p.acc + ACC_STATUS;
+    prefetch2<DT, true>(base, tab, 1, n, pitch, status, qa);
     int i0 = 1;
     for (; i0 + 3 * kPrefetch2 - 1 < n; i0 += 2 * kPrefetch2) {
-        prefetch2<DT, false>(base, tab, i0 + kPrefetch2, n, pitch, qb);
+        prefetch2<DT, false>(base, tab, i0 + kPrefetch2, n, pitch, status, qb);
         walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
-        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch2, n, pitch, qa);
+        prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch2, n, pitch, status, qa);
         walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
     }
     for (; i0 <= n; i0 += 2 * kPrefetch2) {
-        prefetch2<DT, true>(base, tab, i0 + kPrefetch2, n, pitch, qb);
+        prefetch2<DT, true>(base, tab, i0 + kPrefetch2, n, pitch, status, qb);
         walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
         if (i0 + kPrefetch2 > n) break;
-        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch2, n, pitch, qa);
+        prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch2, n, pitch, status, qa);
         walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
     }
     aside = d.frozen || d.qmax > (uint32_t)Q;
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(T, d2_min_blocks<T>()) split_deque2_kernel(con
         if (s < p.S) {
             if (aside) {
                 const unsigned long long idx = atomicAdd(p.acc + ACC_OVERFLOW, 1ull);
-                p.ovf_list[idx] = (int32_t)s;
+                if (index_ok(idx < (unsigned long long)p.S, p.acc + ACC_STATUS)) p.ovf_list[idx] = (int32_t)s;
             } else {
                 sum += c;
                 if (p.out_cost) p.out_cost[s] = c;

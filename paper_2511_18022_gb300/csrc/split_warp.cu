@@ -27,14 +27,15 @@ struct WarpResult {
 // this warp's shared arrays of n + 1 ints each.
 template <typename DT>
 __device__ WarpResult warp_split_scenario(const TourStep *tab, int n, int Q, int L, int g0, const DT *dem,
-                                          long long ld, long long s, int *P, int *g, int16_t *pred = nullptr,
-                                          long long ldp = 0)
+                                          long long ld, long long s, int *P, int *g, unsigned long long *status,
+                                          int16_t *pred = nullptr, long long ldp = 0)
 {
     const int lane = threadIdx.x & 31;
     // Demands in tour order, clamped to Q+1 (anything above Q is infeasible).
     bool neg = false, bad = false;
     for (int i = 1 + lane; i <= n; i += 32) {
-        int q = (int)dem[(long long)(tab[i - 1].row & kRowMask) * ld + s];
+        const int row = tab[i - 1].row & kRowMask;
+        int q = index_ok(row < n && s >= 0 && s < ld, status) ? (int)dem[(long long)row * ld + s] : 0;
         if (q < 0) { neg = true; q = 0; }
         if (q > Q) { bad = true; q = Q + 1; }
         P[i] = q;
@@ -102,7 +103,9 @@ __global__ void __launch_bounds__(128) split_warp_kernel(SplitParams p, const in
     for (long long item = (long long)blockIdx.x * wpb + w; item < total;
          item += (long long)gridDim.x * wpb) {
         const long long s = list ? (long long)list[item] : item;
-        const WarpResult r = warp_split_scenario<DT>(p.tab, n, p.Q, p.L, p.g0, dem, p.ld, s, P, g, p.pred, p.ldp);
+        if (!index_ok(s >= 0 && s < p.S, p.acc + ACC_STATUS)) continue;   // warp-uniform
+        const WarpResult r = warp_split_scenario<DT>(p.tab, n, p.Q, p.L, p.g0, dem, p.ld, s, P, g,
+                                                     p.acc + ACC_STATUS, p.pred, p.ldp);
         if (lane == 0) {
             if (r.neg) status |= ST_NEGATIVE_DEMAND;
             if (r.bad) ++inf; else sum += r.cost;
@@ -134,9 +137,11 @@ __global__ void __launch_bounds__(128) split_warp_batch_kernel(BatchParams b)
     for (long long item = (long long)blockIdx.x * wpb + w; item < total;
          item += (long long)gridDim.x * wpb) {
         const int2 e = b.list[item];
+        if (!index_ok(e.x >= 0 && e.y >= 0 && e.y < b.S, b.acc + BACC_STATUS)) continue;   // warp-uniform
         const TourDev td = b.tours[e.x];
         const WarpResult r = warp_split_scenario<DT>(td.tab, td.n, td.Q, td.L, td.g0,
-                                                     reinterpret_cast<const DT *>(td.demand), td.ld, e.y, P, g);
+                                                     reinterpret_cast<const DT *>(td.demand), td.ld, e.y, P, g,
+                                                     b.acc + BACC_STATUS);
         if (lane == 0) {
             if (r.neg) atomicOr(tacc + 3 * e.x + 2, (unsigned long long)ST_NEGATIVE_DEMAND);
             if (r.bad) atomicAdd(tacc + 3 * e.x + 1, 1ull);

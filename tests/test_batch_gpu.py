@@ -119,9 +119,14 @@ def test_batch_autotune(sp, cv, capped):
     insts, mats = mixed_tours(S, capped=capped)
     tours = [dict(tour=i.tour, dist=i.dist, demand=dev(m), Q=i.Q, L=i.L) for i, m in zip(insts, mats)]
     r = sp.batch_autotune(tours, S)
-    assert r["shapes_timed"] == 6 and r["ms"] > 0
-    assert (r["threads"], r["spt"], r["ring"]) in {(128, 1, 16), (128, 1, 32), (128, 2, 16),
-                                                   (256, 1, 16), (256, 1, 32), (256, 2, 16)}
+    # scenarios per block 32..512 x rings 16 / 32 / 64: every compiled shape timed
+    shapes = {(t, s, g) for t in (32, 64, 128, 256) for s in (1, 2) for g in (16, 32, 64)
+              if not (t == 256 and g == 64) and not (t == 128 and s == 2 and g == 64)
+              and not (t == 256 and s == 2 and g > 16)}
+    assert len(shapes) == 20
+    assert r["shapes_timed"] == 20 and r["ms"] > 0
+    assert (r["threads"], r["spt"], r["ring"]) in shapes
+    assert r["dtype"] in (cv.I16, cv.I32)
     b, tours, outs, res = run_batch(sp, insts, mats, S)
     st = sp.stats()
     assert (st["threads"], st["spt"], st["ring"]) == (r["threads"], r["spt"], r["ring"])
@@ -180,3 +185,15 @@ def test_batched_512_sampled(sp, cv):
         assert res["sum"][t] == int(got[feas].astype(np.int64).sum())
         assert res["infeasible"][t] == int((~feas).sum())
     b.close()
+
+
+def test_batch_autotune_dtype_arm_skips_int16_when_demands_do_not_fit(sp, cv):
+    """The demand-storage arm times int16 and int32 copies of a sample; a
+    demand beyond int16 (here in an int32 batch) leaves only int32."""
+    S = 1000
+    insts, mats = mixed_tours(S)
+    mats32 = [m.astype(np.int32) for m in mats]
+    mats32[2][5, 17] = 40_000                      # above int16; also above Q: infeasible there
+    tours = [dict(tour=i.tour, dist=i.dist, demand=dev(m), Q=i.Q, L=i.L) for i, m in zip(insts, mats32)]
+    r = sp.batch_autotune(tours, S)
+    assert r["dtype"] == cv.I32 and r["shapes_timed"] == 20

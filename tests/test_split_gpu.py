@@ -325,6 +325,28 @@ def test_negative_demand_found_by_a_call_that_did_not_wait(sp, cv):
     sp.check_inputs()                                   # the record was cleared
 
 
+def test_log_callback(sp, cv):
+    """Messages go to the caller's function only: the detail of a failing
+    call (error level) and, at debug level, what each Split ran."""
+    msgs = []
+    sp.set_log(lambda level, text: msgs.append((level, text)), max_level=cv._lib.LOG_DEBUG)
+    inst = make_instance(20, 1, 10, seed=1, Q=30)
+    D = to_dev(np.ones((20, 100), np.int16))
+    sp.split(inst.tour, inst.dist, D, 30, 20)
+    assert any(lvl == cv._lib.LOG_DEBUG and "split n=20 S=100" in t for lvl, t in msgs)
+    with pytest.raises(cv.CvrpsdError):
+        sp.split(inst.tour, inst.dist, D, 30, 0)
+    assert any(lvl == cv._lib.LOG_ERROR and "L = 0" in t for lvl, t in msgs)
+    msgs.clear()
+    sp.set_log(lambda level, text: msgs.append((level, text)), max_level=cv._lib.LOG_ERROR)
+    sp.split(inst.tour, inst.dist, D, 30, 20)
+    assert msgs == []                                   # debug messages filtered out
+    sp.set_log(None)
+    with pytest.raises(cv.CvrpsdError):
+        sp.split(inst.tour, inst.dist, D, 30, 0)
+    assert msgs == []                                   # logging off
+
+
 def test_argument_errors(sp, cv):
     inst = make_instance(20, 1, 10, seed=1, Q=30)
     D = to_dev(np.ones((20, 100), np.int16))
