@@ -57,6 +57,7 @@ extern "C" {
 #define CVRPSD_ERR_DEVICE_STATUS  -5   /* a kernel reported a bad input */
 #define CVRPSD_ERR_NOMEM          -6   /* scratch allocation failed */
 #define CVRPSD_ERR_UNSUPPORTED    -7   /* size beyond the library's limits */
+#define CVRPSD_ERR_TIMEOUT        -8   /* a device-side wait gave up (bounded polls) */
 
 #define CVRPSD_I16  2
 #define CVRPSD_I32  4
@@ -395,8 +396,9 @@ int cvrpsd_gather_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t rows, i
  * fractional part of the cumulative mean demand / Q) of the customer there;
  * layer 1 (256 units, ReLU) runs per position and is mean-pooled, the tour's
  * closed length joins (see cvrpsd_surrogate_set_scale), layer 2 (256, ReLU)
- * and layer 3 (scalar) follow. BF16
- * weights, FP32 accumulation, Adam on FP32 master weights. */
+ * and layer 3 (scalar) follow. BF16 weights and per-position features, FP32
+ * accumulation, Adam on FP32 master weights. Layer 1's forward pass runs on
+ * the tensor cores (tcgen05 MMAs, accumulators in tensor memory). */
 typedef struct cvrpsd_surrogate cvrpsd_surrogate;
 #define CVRPSD_SURROGATE_PARAMS 67841
 
@@ -414,7 +416,9 @@ int cvrpsd_surrogate_predict(cvrpsd_surrogate *sur, const int32_t *d_tours, int3
 int cvrpsd_surrogate_train_step(cvrpsd_surrogate *sur, const int32_t *d_tours, int32_t T,
                                 const float *d_target, float lr, float *d_loss, void *stream);
 /* Gradient of that loss w.r.t. all parameters, without updating them
- * (synchronous): h_grad HOST [CVRPSD_SURROGATE_PARAMS], h_loss HOST or NULL. */
+ * (synchronous): h_grad HOST [CVRPSD_SURROGATE_PARAMS], h_loss HOST or NULL.
+ * Also reports CVRPSD_ERR_TIMEOUT if a tensor-core kernel of this network
+ * (this or an earlier call) gave up waiting for its MMAs. */
 int cvrpsd_surrogate_gradients(cvrpsd_surrogate *sur, const int32_t *d_tours, int32_t T,
                                const float *d_target, float *h_grad, float *h_loss);
 /* The tour-length input becomes (closed tour length - len_mean) / len_sd

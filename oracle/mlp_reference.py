@@ -6,7 +6,8 @@ not part of the paper's method: it screens local-search neighbours before
 the exact Split evaluates them.
 
 Network (width H = 256), for a tour sigma_1..sigma_n of an instance with
-customer features (x, y, mean demand mu, demand sd), capacity Q and distances c:
+customer features (x, y, mean demand mu, demand sd), capacity Q and distances c
+(with bf16=True the weights and phi are rounded to bfloat16 first):
     phi_k = (x/1000, y/1000, mu/Q, sd/Q, frac(sum_{t<=k} mu_{sigma_t} / Q))
     h_k   = relu(W1 phi_k + b1)
     z     = (1/n) sum_k h_k
@@ -63,11 +64,14 @@ def features(tours, cust, dist, Q, len_mean=0.0, len_sd=None):
 
 
 def forward(p, phi, t, bf16=False):
-    """Network outputs and the intermediates the backward pass needs."""
+    """Network outputs and the intermediates the backward pass needs. With
+    bf16 the weights and the per-position features are rounded to bfloat16
+    first (the library's operands); everything else stays float64."""
     W1, b1, W2, b2, w3, b3 = unpack(p)
     if bf16:
         W1, b1, W2, b2, w3 = (to_bf16(a) for a in (W1, b1, W2, b2, w3))
         b3 = to_bf16(np.array([b3]))[0]
+        phi = to_bf16(phi)
     pre = np.einsum("tkf,jf->tkj", phi, W1) + b1          # [T][n][H]
     z = np.maximum(pre, 0.0).mean(axis=1)                # [T][H]
     zt = np.concatenate([z, t[:, None]], axis=1)          # [T][H+1]
@@ -79,6 +83,8 @@ def forward(p, phi, t, bf16=False):
 
 def loss_and_grad(p, phi, t, target, bf16=False):
     y, c = forward(p, phi, t, bf16)
+    if bf16:
+        phi = to_bf16(phi)
     T, n, _ = phi.shape
     err = y - np.asarray(target, dtype=np.float64)
     loss = float((err ** 2).mean())

@@ -19,6 +19,7 @@ ERR_CUDA = -4
 ERR_DEVICE_STATUS = -5
 ERR_NOMEM = -6
 ERR_UNSUPPORTED = -7
+ERR_TIMEOUT = -8
 I16 = 2
 I32 = 4
 MAX_N = 8191

@@ -33,6 +33,7 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("search.cu", [], "search.o"),
     ("seqpar.cu", [], "seqpar.o"),
     ("mlp.cu", [], "mlp.o"),
+    ("mlp_tc.cu", [], "mlp_tc.o"),
     ("search_api.cu", [], "search_api.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("probe.cu", [], "probe.o"),

@@ -166,6 +166,7 @@ const char *cvrpsd_strerror(int code)
     case CVRPSD_ERR_DEVICE_STATUS: return "a kernel reported invalid input";
     case CVRPSD_ERR_NOMEM: return "out of device memory";
     case CVRPSD_ERR_UNSUPPORTED: return "size beyond the library's limits";
+    case CVRPSD_ERR_TIMEOUT: return "a device-side wait gave up";
     default: return "unknown status";
     }
 }

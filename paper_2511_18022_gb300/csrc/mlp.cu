@@ -1,5 +1,9 @@
 // Surrogate network for screening local-search neighbours: training and
-// inference kernels. BF16 weights, FP32 activations and accumulation.
+// inference kernels. BF16 weights and per-position features, FP32
+// activations and accumulation. Layer 1's forward pass runs on the tensor
+// cores (mlp_tc.cu); this file holds the rest: the backward pass of layer 1
+// (which recomputes the pre-activations from the same BF16 operands), the
+// layer 2 products, the output layer, the loss and Adam.
 //
 // Architecture (width H = 256):
 //   per position k of a tour:  phi_k = (x, y, mu / Q, sd / Q, frac(cum_k / Q))
@@ -64,12 +68,13 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
             for (int q = 0; q < w; ++q) off += s_part[q];
             const float cum = off + v;
             if (k < n) {
+                // features in BF16, as the tensor-core forward pass takes them
                 float *f = feat + 5 * k;
-                f[0] = a.cust[(c - 1) * 4 + 0];
-                f[1] = a.cust[(c - 1) * 4 + 1];
-                f[2] = m;
-                f[3] = a.cust[(c - 1) * 4 + 3];
-                f[4] = cum - floorf(cum);
+                f[0] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 0]));
+                f[1] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 1]));
+                f[2] = __bfloat162float(__float2bfloat16_rn(m));
+                f[3] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 3]));
+                f[4] = __bfloat162float(__float2bfloat16_rn(cum - floorf(cum)));
             }
             __syncthreads();
             if (j == kMlpH - 1) s_carry = cum;
@@ -306,11 +311,8 @@ cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U,
                         float *dy, float *loss, cudaStream_t st)
 {
     const int T = l1.T;
-    const size_t smem = (size_t)l1.n * 5 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(mlp_layer1_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = mlp_layer1_tc(l1, l1.sm_count > 0 ? l1.sm_count : 1, st);
     if (e != cudaSuccess) return e;
-    mlp_layer1_kernel<false><<<T < 16384 ? T : 16384, kMlpH, smem, st>>>(l1);
     gemm_xwt_kernel<<<grid2(kMlpH, T), 256, 0, st>>>(l1.zt, T, kMlpIn2, kMlpIn2, wt.w2, kMlpH, kMlpIn2, wt.b2, U, kMlpH,
                                                       1);
     mlp_out_kernel<<<(T + 7) / 8, 256, 0, st>>>(U, T, wt.w3, wt.b3, y, target, dy, loss);

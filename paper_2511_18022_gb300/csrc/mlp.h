@@ -35,7 +35,13 @@ struct MlpLayer1Args {
     float *zt;                             // device [T][H+1]: pooled features and tour length
     const float *dzt;                      // backward: gradient of zt
     float *gw1, *gb1;                      // backward: accumulated gradients
+    unsigned int *err;                     // device word: set if a tensor-core wait gave up
+    int sm_count;                          // SMs of the device (grid of the tensor-core kernel)
 };
+
+// Layer 1 forward (features, W1, ReLU, mean pool; writes zt) on the tensor
+// cores: tcgen05 MMAs with the accumulators in tensor memory (mlp_tc.cu).
+cudaError_t mlp_layer1_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st);
 
 cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U, float *y, const float *target,
                         float *dy, float *loss, cudaStream_t st);

@@ -233,6 +233,7 @@ struct cvrpsd_surrogate {
     long long cap = 0;             // workspace rows
     float *d_zt = nullptr, *d_U = nullptr, *d_y = nullptr, *d_dy = nullptr, *d_dU = nullptr, *d_dzt = nullptr;
     float *d_loss = nullptr;
+    unsigned int *d_err = nullptr;  // set by a tensor-core kernel whose wait gave up
     int step = 0;
     float len_mean = 0.0f, len_inv_sd = 1.0f;
 };
@@ -244,7 +245,7 @@ void sur_free(cvrpsd_surrogate *s)
     if (!s) return;
     for (void *p : {(void *)s->d_cust, (void *)s->d_dist, (void *)s->d_p, (void *)s->d_g, (void *)s->d_m,
                     (void *)s->d_v, (void *)s->d_pb, (void *)s->d_zt, (void *)s->d_U, (void *)s->d_y,
-                    (void *)s->d_dy, (void *)s->d_dU, (void *)s->d_dzt, (void *)s->d_loss})
+                    (void *)s->d_dy, (void *)s->d_dU, (void *)s->d_dzt, (void *)s->d_loss, (void *)s->d_err})
         if (p) cudaFree(p);
     delete s;
 }
@@ -295,7 +296,20 @@ MlpLayer1Args layer1_of(const cvrpsd_surrogate *s, const int32_t *tours, int T)
     a.len_mean = s->len_mean;
     a.len_inv_sd = s->len_inv_sd;
     a.zt = s->d_zt;
+    a.err = s->d_err;
+    a.sm_count = s->ctx->sm_count > 0 ? s->ctx->sm_count : 1;
     return a;
+}
+
+// A tensor-core kernel of an earlier call on this network gave up waiting
+// for its MMAs (read after the device has finished that work).
+int sur_device_error(cvrpsd_surrogate *s)
+{
+    cvrpsd_ctx *ctx = s->ctx;
+    unsigned int h = 0;
+    CK(cudaMemcpy(&h, s->d_err, sizeof(h), cudaMemcpyDeviceToHost), "read status");
+    if (h) return fail(ctx, CVRPSD_ERR_TIMEOUT, "a tensor-core wait of the surrogate gave up");
+    return CVRPSD_OK;
 }
 
 int sur_check(cvrpsd_surrogate *s, const int32_t *d_tours, int32_t T)
@@ -372,6 +386,8 @@ int cvrpsd_surrogate_create(cvrpsd_ctx *ctx, int32_t n, const float *cust, const
     SK(dev_alloc(ctx, &s->d_v, sizeof(float) * kMlpParams), "cudaMalloc");
     SK(dev_alloc(ctx, &s->d_pb, sizeof(__nv_bfloat16) * kMlpParams), "cudaMalloc");
     SK(dev_alloc(ctx, &s->d_loss, sizeof(float)), "cudaMalloc");
+    SK(dev_alloc(ctx, &s->d_err, sizeof(unsigned int)), "cudaMalloc");
+    SK(cudaMemset(s->d_err, 0, sizeof(unsigned int)), "memset");
     SK(cudaMemcpy(s->d_cust, c.data(), sizeof(float) * n * 4, cudaMemcpyHostToDevice), "upload");
     SK(cudaMemcpy(s->d_dist, dist, sizeof(int32_t) * N1 * N1, cudaMemcpyHostToDevice), "upload");
     SK(cudaMemcpy(s->d_p, p.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice), "upload");
@@ -449,7 +465,7 @@ int cvrpsd_surrogate_gradients(cvrpsd_surrogate *s, const int32_t *d_tours, int3
     if (rc) return rc;
     CK(cudaMemcpy(h_grad, s->d_g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost), "read gradient");
     if (h_loss) CK(cudaMemcpy(h_loss, s->d_loss, sizeof(float), cudaMemcpyDeviceToHost), "read loss");
-    return CVRPSD_OK;
+    return sur_device_error(s);
 }
 
 int cvrpsd_surrogate_set_scale(cvrpsd_surrogate *s, float len_mean, float len_sd)

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_strerror_and_version(lib):
-    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
         assert lib.cvrpsd_strerror(code).decode()
     assert "sm_103a" in cv.cvrpsd_version()
 
