@@ -124,46 +124,9 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
 }
 
 // ---------------------------------------------------------------- GEMMs
-// 32 x 32 output tile per block of 256 threads (4 outputs per thread), the
-// reduction dimension in chunks of 32 through shared memory.
-
-// out[b][o] = act(sum_k X[b][k] W[o][k] + bias[o])      X fp32, W bf16
-__global__ void __launch_bounds__(256) gemm_xwt_kernel(const float *X, int B, int Kd, int ldx,
-                                                       const __nv_bfloat16 *W, int N, int ldw, const __nv_bfloat16 *bias,
-                                                       float *out, int ldo, int relu)
-{
-    __shared__ float sx[32][33], sw[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // ty 0..7
-    const int b0 = blockIdx.y * 32, o0 = blockIdx.x * 32;
-    float acc[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < Kd; k0 += 32) {
-        for (int r = ty; r < 32; r += 8) {
-            const int b = b0 + r, o = o0 + r, k = k0 + tx;
-            sx[r][tx] = (b < B && k < Kd) ? X[(long long)b * ldx + k] : 0.0f;
-            sw[r][tx] = (o < N && k < Kd) ? __bfloat162float(W[(long long)o * ldw + k]) : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const float wv = sw[tx][k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += sx[ty + 8 * q][k] * wv;
-        }
-        __syncthreads();
-    }
-    const int o = o0 + tx;
-    if (o >= N) return;
-    const float bo = bias ? __bfloat162float(bias[o]) : 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int b = b0 + ty + 8 * q;
-        if (b < B) {
-            float v = acc[q] + bo;
-            if (relu) v = fmaxf(v, 0.0f);
-            out[(long long)b * ldo + o] = v;
-        }
-    }
-}
+// Backward-pass products on the CUDA cores: 32 x 32 output tile per block of
+// 256 threads (4 outputs per thread), the reduction dimension in chunks of 32
+// through shared memory.
 
 // out[b][k] = sum_o G[b][o] W[o][k]                     G fp32, W bf16 [N][ldw]
 __global__ void __launch_bounds__(256) gemm_gw_kernel(const float *G, int B, int N, int ldg, const __nv_bfloat16 *W,
@@ -199,18 +162,22 @@ __global__ void __launch_bounds__(256) gemm_gw_kernel(const float *G, int B, int
 }
 
 // out[o][k] += sum_b G[b][o] X[b][k]                    G, X fp32 (weight gradient)
+// The batch splits into slabs of kGtxSlab rows (blockIdx.z), each adding its
+// partial sums with atomics, so that a large batch fills the GPU.
+constexpr int kGtxSlab = 512;
 __global__ void __launch_bounds__(256) gemm_gtx_kernel(const float *G, int B, int N, int ldg, const float *X, int Kd,
                                                        int ldx, float *out, int ldo)
 {
     __shared__ float sg[32][33], sx[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int bz0 = blockIdx.z * kGtxSlab, bz1 = min(B, bz0 + kGtxSlab);
     float acc[4] = {0, 0, 0, 0};
-    for (int b0 = 0; b0 < B; b0 += 32) {
+    for (int b0 = bz0; b0 < bz1; b0 += 32) {
         for (int r = ty; r < 32; r += 8) {
             const int b = b0 + r;
-            sg[r][tx] = (b < B && o0 + tx < N) ? G[(long long)b * ldg + o0 + tx] : 0.0f;
-            sx[r][tx] = (b < B && k0 + tx < Kd) ? X[(long long)b * ldx + k0 + tx] : 0.0f;
+            sg[r][tx] = (b < bz1 && o0 + tx < N) ? G[(long long)b * ldg + o0 + tx] : 0.0f;
+            sx[r][tx] = (b < bz1 && k0 + tx < Kd) ? X[(long long)b * ldx + k0 + tx] : 0.0f;
         }
         __syncthreads();
 #pragma unroll 8
@@ -226,7 +193,7 @@ __global__ void __launch_bounds__(256) gemm_gtx_kernel(const float *G, int B, in
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int o = o0 + ty + 8 * q;
-        if (o < N) out[(long long)o * ldo + k] += acc[q];
+        if (o < N) atomicAdd(out + (long long)o * ldo + k, acc[q]);
     }
 }
 
@@ -272,14 +239,16 @@ __global__ void mlp_out_backward_kernel(const float *U, int B, const float *dy, 
     if (j == 0) atomicAdd(gb3, accb);
 }
 
-// g_b2[j] += sum_b dU[b][j]
+// g_b2[j] += sum_b dU[b][j]: blocks take 64-row slabs, one atomic per column
+// and slab.
 __global__ void colsum_kernel(const float *G, int B, int N, int ldg, float *out)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
+    const int b0 = blockIdx.y * 64, b1 = min(B, b0 + 64);
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += G[(long long)b * ldg + j];
-    out[j] += s;
+    for (int b = b0; b < b1; ++b) s += G[(long long)b * ldg + j];
+    atomicAdd(out + j, s);
 }
 
 // ---------------------------------------------------------------- Adam
@@ -313,8 +282,8 @@ cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U,
     const int T = l1.T;
     cudaError_t e = mlp_layer1_tc(l1, l1.sm_count > 0 ? l1.sm_count : 1, st);
     if (e != cudaSuccess) return e;
-    gemm_xwt_kernel<<<grid2(kMlpH, T), 256, 0, st>>>(l1.zt, T, kMlpIn2, kMlpIn2, wt.w2, kMlpH, kMlpIn2, wt.b2, U, kMlpH,
-                                                      1);
+    e = mlp_layer2_tc(l1.zt, T, wt.w2, wt.b2, U, l1.err, st);
+    if (e != cudaSuccess) return e;
     mlp_out_kernel<<<(T + 7) / 8, 256, 0, st>>>(U, T, wt.w3, wt.b3, y, target, dy, loss);
     return cudaGetLastError();
 }
@@ -326,8 +295,10 @@ cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const fl
     float *gw1 = grad + kOffW1, *gb1 = grad + kOffB1, *gw2 = grad + kOffW2, *gb2 = grad + kOffB2;
     float *gw3 = grad + kOffW3, *gb3 = grad + kOffB3;
     mlp_out_backward_kernel<<<T < 512 ? T : 512, kMlpH, 0, st>>>(U, T, dy, wt.w3, dU, gw3, gb3);
-    gemm_gtx_kernel<<<grid2(kMlpIn2, kMlpH), 256, 0, st>>>(dU, T, kMlpH, kMlpH, l1.zt, kMlpIn2, kMlpIn2, gw2, kMlpIn2);
-    colsum_kernel<<<1, kMlpH, 0, st>>>(dU, T, kMlpH, kMlpH, gb2);
+    dim3 g3 = grid2(kMlpIn2, kMlpH);
+    g3.z = (unsigned)((T + kGtxSlab - 1) / kGtxSlab);
+    gemm_gtx_kernel<<<g3, 256, 0, st>>>(dU, T, kMlpH, kMlpH, l1.zt, kMlpIn2, kMlpIn2, gw2, kMlpIn2);
+    colsum_kernel<<<dim3(1, (unsigned)((T + 63) / 64)), kMlpH, 0, st>>>(dU, T, kMlpH, kMlpH, gb2);
     gemm_gw_kernel<<<grid2(kMlpIn2, T), 256, 0, st>>>(dU, T, kMlpH, kMlpH, wt.w2, kMlpIn2, kMlpIn2, dzt, kMlpIn2);
     MlpLayer1Args b = l1;
     b.dzt = dzt;

@@ -1,4 +1,5 @@
-// Layer 1 of the surrogate network on the tensor cores (tcgen05, TMEM).
+// Layers 1 and 2 of the surrogate network's forward pass on the tensor cores
+// (tcgen05, TMEM). Layer 1:
 //
 // Per tour the layer is a small matrix product: the pre-activations of the
 // H = 256 hidden units at the n positions are W1' (H x 16) times F' (16 x n),
@@ -26,6 +27,7 @@
 #include <stdint.h>
 
 #include "mlp.h"
+#include "tcgen05.h"
 
 namespace cvrpsd {
 
@@ -35,84 +37,9 @@ constexpr int kTcThreads = 256;          // eight warps
 constexpr int kTcChunk = 256;            // positions per MMA (N <= 256)
 constexpr int kTcK = 16;                 // one kind::f16 MMA step
 constexpr uint32_t kTmemCols = 512;      // two 128 x 256 FP32 accumulators
-constexpr uint32_t kPollLimit = 1u << 26;
 // Shared memory the kernel asks for beyond its static arrays: enough that a
 // second CTA cannot share the SM (and its tensor memory).
 constexpr size_t kTcSmemPad = 120 * 1024;
-
-// Byte offset of element (row, k) of a K-major, unswizzled BF16 operand of
-// 16 columns: 8-row x 16-byte core matrices, two per 8-row group along K.
-__device__ __forceinline__ uint32_t kmajor_offset(int row, int k)
-{
-    return (uint32_t)(((row >> 3) * 2 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor (sm_100 format): start address, leading
-// byte offset (between core matrices along K), stride byte offset (between
-// 8-row groups), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, M = 128, N = n_cols.
-__device__ __forceinline__ uint32_t instr_desc(uint32_t n_cols)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((n_cols >> 3) << 17) | ((128u >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, bool acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)acc) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-
-// Poll the mbarrier's phase `parity` at most kPollLimit times.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
-{
-    for (uint32_t it = 0; it < kPollLimit; ++it) {
-        uint32_t done = 0;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1Args a)
 {
@@ -139,26 +66,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
         __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
         if (k < kMlpIn1) v = a.w1[h * kMlpIn1 + k];
         else if (k == kMlpIn1) v = a.b1[h];
-        *reinterpret_cast<__nv_bfloat16 *>(s_w1 + kmajor_offset(h, k)) = v;
+        *reinterpret_cast<__nv_bfloat16 *>(s_w1 + tc::kmajor_offset(h, k, 2)) = v;
     }
     if (j == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc::mbar_init(mbar);
         s_abort = 0;
     }
-    if (w == 0) {
-        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_tmem);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
-                     "r"(kTmemCols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (w == 0) tc::tmem_alloc((uint32_t)__cvta_generic_to_shared(&s_tmem), kTmemCols);
+    tc::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const uint64_t a_desc0 = smem_desc(w1_s, 128, 256);
-    const uint64_t a_desc1 = smem_desc(w1_s + 16 * 256, 128, 256);   // hidden units 128..255
-    const uint64_t b_desc = smem_desc(f_s, 128, 256);
+    const uint64_t a_desc0 = tc::smem_desc(w1_s, 128, 256);
+    const uint64_t a_desc1 = tc::smem_desc(w1_s + 16 * 256, 128, 256);   // hidden units 128..255
+    const uint64_t b_desc = tc::smem_desc(f_s, 128, 256);
     // This warp's TMEM rows: lanes 32 (w % 4) .. +31 of accumulator w / 4.
     const int half = w >> 2;
     const uint32_t t_row = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(half * kTcChunk);
@@ -216,35 +137,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
                     const uint32_t hi = __bfloat16_as_ushort(f[half_k * 8 + 2 * q + 1]);
                     pw[q] = lo | (hi << 16);
                 }
-                *reinterpret_cast<uint4 *>(s_f + kmajor_offset(j, half_k * 8)) = pack;
+                *reinterpret_cast<uint4 *>(s_f + tc::kmajor_offset(j, half_k * 8, 2)) = pack;
             }
             __syncthreads();
             if (j == kTcThreads - 1) s_carry = cum;
             // operands visible to the tensor cores, previous TMEM reads retired
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            tc::fence_operands();
+            tc::fence_before_sync();
             __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc::fence_after_sync();
             const int cnt = min(kTcChunk, n - k0);
             const uint32_t ncols = (uint32_t)((cnt + 31) / 32 * 32);
             if (j == 0) {
-                const uint32_t idesc = instr_desc(ncols);
-                mma_bf16(tmem, a_desc0, b_desc, idesc, false);
-                mma_bf16(tmem + kTcChunk, a_desc1, b_desc, idesc, false);
-                mma_commit(mbar);
+                const uint32_t idesc = tc::instr_desc(ncols);
+                tc::mma_bf16(tmem, a_desc0, b_desc, idesc, false);
+                tc::mma_bf16(tmem + kTcChunk, a_desc1, b_desc, idesc, false);
+                tc::mma_commit(mbar);
             }
-            if (!mbar_wait(mbar, parity)) {
+            if (!tc::mbar_wait(mbar, parity)) {
                 atomicOr(a.err, 1u);
                 s_abort = 1;
             }
             parity ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc::fence_after_sync();
             __syncthreads();
             if (s_abort) break;
             // ReLU and sum along this thread's row (positions past n hold 0)
             for (uint32_t col = 0; col < ncols; col += 32) {
                 float r[32];
-                tmem_ld32(t_row + col, r);
+                tc::tmem_ld32(t_row + col, r);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) acc += fmaxf(r[q], 0.0f);
             }
@@ -263,13 +184,121 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
         }
         a.zt[(long long)t * kMlpIn2 + h] = acc / (float)n;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::fence_before_sync();
     __syncthreads();
-    if (w == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (w == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------- layer 2
+//
+// U = relu([z; t] W2^T + b2) for a tile of 128 tours and 128 of the 256
+// hidden units: M = 128 tours, N = 128, K = 257 inputs + 1 (the bias rides
+// in W2' as column 257 against a constant 1) padded to 272 = 17 MMA steps.
+// The pooled inputs are FP32; each is split into BF16 hi + lo parts
+// (hi = bf16(v), lo = bf16(v - hi)) and both products are accumulated, so the
+// result keeps about 16 significant bits of the inputs against the exact
+// BF16 weights: the FP32 layer's accuracy on the tensor cores.
+constexpr int kL2K = 272;                 // padded K
+constexpr int kL2Kc = kL2K / 8;           // 16-byte core-matrix columns per row group
+constexpr int kL2Rows = 128;              // tours (M) and hidden units (N) per CTA
+constexpr size_t kL2Operand = (size_t)kL2Rows * kL2K * 2;   // one 128 x 272 BF16 operand
+constexpr size_t kL2Smem = 3 * kL2Operand;                  // A hi, A lo, B
+constexpr uint32_t kL2TmemCols = 128;
+
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const float *zt, int T,
+                                                                      const __nv_bfloat16 *w2,
+                                                                      const __nv_bfloat16 *b2, float *U,
+                                                                      unsigned int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];   // A hi | A lo | B
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    unsigned char *a_hi = smem, *a_lo = smem + kL2Operand, *bw = smem + 2 * kL2Operand;
+    const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+    const int t0 = blockIdx.x * kL2Rows, o0 = blockIdx.y * kL2Rows;
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    // B = W2' rows o0 .. o0 + 127: weights, bias at column 257, zeros after
+    for (int e = j; e < kL2Rows * kL2K; e += kTcThreads) {
+        const int r = e / kL2K, k = e % kL2K;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+        if (k < kMlpIn2) v = w2[(long long)(o0 + r) * kMlpIn2 + k];
+        else if (k == kMlpIn2) v = b2[o0 + r];
+        *reinterpret_cast<__nv_bfloat16 *>(bw + tc::kmajor_offset(r, k, kL2Kc)) = v;
+    }
+    // A = [z; t; 1] of tours t0 .. t0 + 127 split into BF16 hi and lo parts
+    for (int e = j; e < kL2Rows * kL2K; e += kTcThreads) {
+        const int r = e / kL2K, k = e % kL2K;
+        const int t = t0 + r;
+        float v = 0.0f;
+        if (t < T) {
+            if (k < kMlpIn2) v = zt[(long long)t * kMlpIn2 + k];
+            else if (k == kMlpIn2) v = 1.0f;
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const uint32_t off = tc::kmajor_offset(r, k, kL2Kc);
+        *reinterpret_cast<__nv_bfloat16 *>(a_hi + off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(a_lo + off) = lo;
+    }
+    if (j == 0) tc::mbar_init(mbar);
+    if (w == 0) tc::tmem_alloc((uint32_t)__cvta_generic_to_shared(&s_tmem), kL2TmemCols);
+    tc::fence_operands();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (j == 0) {
+        const uint32_t idesc = tc::instr_desc(kL2Rows);
+        const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(a_hi);
+        const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(a_lo);
+        const uint32_t sb = (uint32_t)__cvta_generic_to_shared(bw);
+        const uint32_t sbo = kL2Kc * 128;
+        for (int step = 0; step < kL2K / 16; ++step) {
+            const uint32_t koff = (uint32_t)step * 256;     // two 16-byte core-matrix columns per step
+            const uint64_t bd = tc::smem_desc(sb + koff, 128, sbo);
+            tc::mma_bf16(tmem, tc::smem_desc(sa_hi + koff, 128, sbo), bd, idesc, step > 0);
+            tc::mma_bf16(tmem, tc::smem_desc(sa_lo + koff, 128, sbo), bd, idesc, true);
+        }
+        tc::mma_commit(mbar);
+    }
+    const bool ok = tc::mbar_wait(mbar, 0);
+    if (!ok && lane == 0) atomicOr(err, 1u);
+    tc::fence_after_sync();
+    __syncthreads();
+    if (ok) {
+        // warp w: tours (lanes) 32 (w % 4) .., hidden columns 64 (w / 4) .. + 63
+        const int t = t0 + 32 * (w & 3) + lane;
+        const uint32_t row = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (w >> 2));
+#pragma unroll
+        for (int c = 0; c < 64; c += 32) {
+            float r[32];
+            tc::tmem_ld32(row + c, r);
+            if (t < T) {
+                float *out = U + (long long)t * kMlpH + o0 + 64 * (w >> 2) + c;
+#pragma unroll
+                for (int q = 0; q < 32; q += 4)
+                    *reinterpret_cast<float4 *>(out + q) = make_float4(fmaxf(r[q], 0.0f), fmaxf(r[q + 1], 0.0f),
+                                                                       fmaxf(r[q + 2], 0.0f), fmaxf(r[q + 3], 0.0f));
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tmem, kL2TmemCols);
 }
 
 }  // namespace
+
+cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const __nv_bfloat16 *b2, float *U,
+                          unsigned int *err, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(mlp_layer2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kL2Smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((T + kL2Rows - 1) / kL2Rows), kMlpH / kL2Rows);
+    mlp_layer2_tc_kernel<<<grid, kTcThreads, kL2Smem, st>>>(zt, T, w2, b2, U, err);
+    return cudaGetLastError();
+}
 
 cudaError_t mlp_layer1_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st)
 {
