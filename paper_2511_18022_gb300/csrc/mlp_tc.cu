@@ -191,19 +191,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
 
 // ---------------------------------------------------------------- layer 2
 //
-// U = relu([z; t] W2^T + b2) for a tile of 128 tours and 128 of the 256
-// hidden units: M = 128 tours, N = 128, K = 257 inputs + 1 (the bias rides
-// in W2' as column 257 against a constant 1) padded to 272 = 17 MMA steps.
-// The pooled inputs are FP32; each is split into BF16 hi + lo parts
-// (hi = bf16(v), lo = bf16(v - hi)) and both products are accumulated, so the
-// result keeps about 16 significant bits of the inputs against the exact
-// BF16 weights: the FP32 layer's accuracy on the tensor cores.
+// U = relu([z; t] W2^T + b2) for a tile of 128 tours and 64 of the 256 hidden
+// units: M = 128 tours, N = 64, K = 257 inputs + 1 (the bias rides in W2' as
+// column 257 against a constant 1) padded to 272 = 17 MMA steps. The pooled
+// inputs are FP32; each is split into BF16 hi + lo parts (hi = bf16(v),
+// lo = bf16(v - hi)) and both products are accumulated, so the result keeps
+// about 16 significant bits of the inputs against the exact BF16 weights:
+// the FP32 layer's accuracy on the tensor cores. Operands are staged 16 bytes
+// (one core-matrix row) per store.
 constexpr int kL2K = 272;                 // padded K
 constexpr int kL2Kc = kL2K / 8;           // 16-byte core-matrix columns per row group
-constexpr int kL2Rows = 128;              // tours (M) and hidden units (N) per CTA
-constexpr size_t kL2Operand = (size_t)kL2Rows * kL2K * 2;   // one 128 x 272 BF16 operand
-constexpr size_t kL2Smem = 3 * kL2Operand;                  // A hi, A lo, B
-constexpr uint32_t kL2TmemCols = 128;
+constexpr int kL2M = 128;                 // tours per CTA
+constexpr int kL2N = 64;                  // hidden units per CTA
+constexpr size_t kL2A = (size_t)kL2M * kL2K * 2;   // one 128 x 272 BF16 operand
+constexpr size_t kL2B = (size_t)kL2N * kL2K * 2;
+constexpr size_t kL2Smem = 2 * kL2A + kL2B;        // A hi, A lo, B
+constexpr uint32_t kL2TmemCols = 64;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const float *zt, int T,
                                                                       const __nv_bfloat16 *w2,
@@ -213,32 +221,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const floa
     extern __shared__ __align__(128) unsigned char smem[];   // A hi | A lo | B
     __shared__ __align__(8) unsigned long long s_mbar;
     __shared__ uint32_t s_tmem;
-    unsigned char *a_hi = smem, *a_lo = smem + kL2Operand, *bw = smem + 2 * kL2Operand;
+    unsigned char *a_hi = smem, *a_lo = smem + kL2A, *bw = smem + 2 * kL2A;
     const int j = threadIdx.x, lane = j & 31, w = j >> 5;
-    const int t0 = blockIdx.x * kL2Rows, o0 = blockIdx.y * kL2Rows;
+    const int t0 = blockIdx.x * kL2M, o0 = blockIdx.y * kL2N;
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
-    // B = W2' rows o0 .. o0 + 127: weights, bias at column 257, zeros after
-    for (int e = j; e < kL2Rows * kL2K; e += kTcThreads) {
-        const int r = e / kL2K, k = e % kL2K;
-        __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-        if (k < kMlpIn2) v = w2[(long long)(o0 + r) * kMlpIn2 + k];
-        else if (k == kMlpIn2) v = b2[o0 + r];
-        *reinterpret_cast<__nv_bfloat16 *>(bw + tc::kmajor_offset(r, k, kL2Kc)) = v;
-    }
-    // A = [z; t; 1] of tours t0 .. t0 + 127 split into BF16 hi and lo parts
-    for (int e = j; e < kL2Rows * kL2K; e += kTcThreads) {
-        const int r = e / kL2K, k = e % kL2K;
-        const int t = t0 + r;
-        float v = 0.0f;
-        if (t < T) {
-            if (k < kMlpIn2) v = zt[(long long)t * kMlpIn2 + k];
-            else if (k == kMlpIn2) v = 1.0f;
+    // B = W2' rows o0 .. o0 + 63: weights, bias at column 257, zeros after;
+    // item = (row, group of 8 columns)
+    for (int e = j; e < kL2N * kL2Kc; e += kTcThreads) {
+        const int r = e / kL2Kc, g = e % kL2Kc;
+        uint32_t pw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __nv_bfloat16 v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 8 * g + 2 * q + h;
+                v[h] = k < kMlpIn2 ? w2[(long long)(o0 + r) * kMlpIn2 + k]
+                                   : (k == kMlpIn2 ? b2[o0 + r] : __float2bfloat16_rn(0.0f));
+            }
+            pw[q] = pack_bf16x2(v[0], v[1]);
         }
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const uint32_t off = tc::kmajor_offset(r, k, kL2Kc);
-        *reinterpret_cast<__nv_bfloat16 *>(a_hi + off) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(a_lo + off) = lo;
+        *reinterpret_cast<uint4 *>(bw + tc::kmajor_offset(r, 8 * g, kL2Kc)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+    }
+    // A = [z; t; 1] of tours t0 .. t0 + 127, split into BF16 hi and lo parts
+    for (int e = j; e < kL2M * kL2Kc; e += kTcThreads) {
+        const int r = e / kL2Kc, g = e % kL2Kc;
+        const int t = t0 + r;
+        uint32_t ph[4], pl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __nv_bfloat16 hi[2], lo[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 8 * g + 2 * q + h;
+                float v = 0.0f;
+                if (t < T) v = k < kMlpIn2 ? zt[(long long)t * kMlpIn2 + k] : (k == kMlpIn2 ? 1.0f : 0.0f);
+                hi[h] = __float2bfloat16_rn(v);
+                lo[h] = __float2bfloat16_rn(v - __bfloat162float(hi[h]));
+            }
+            ph[q] = pack_bf16x2(hi[0], hi[1]);
+            pl[q] = pack_bf16x2(lo[0], lo[1]);
+        }
+        const uint32_t off = tc::kmajor_offset(r, 8 * g, kL2Kc);
+        *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+        *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
     }
     if (j == 0) tc::mbar_init(mbar);
     if (w == 0) tc::tmem_alloc((uint32_t)__cvta_generic_to_shared(&s_tmem), kL2TmemCols);
@@ -248,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const floa
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
     if (j == 0) {
-        const uint32_t idesc = tc::instr_desc(kL2Rows);
+        const uint32_t idesc = tc::instr_desc(kL2N);
         const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(a_hi);
         const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(a_lo);
         const uint32_t sb = (uint32_t)__cvta_generic_to_shared(bw);
@@ -265,16 +291,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const floa
     if (!ok && lane == 0) atomicOr(err, 1u);
     tc::fence_after_sync();
     __syncthreads();
-    if (ok) {
-        // warp w: tours (lanes) 32 (w % 4) .., hidden columns 64 (w / 4) .. + 63
-        const int t = t0 + 32 * (w & 3) + lane;
-        const uint32_t row = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (w >> 2));
+    if (ok && w < 4) {
+        // warp w: tours (lanes) 32 w .. 32 w + 31, all 64 hidden columns
+        const int t = t0 + 32 * w + lane;
+        const uint32_t row = tmem + ((uint32_t)(32 * w) << 16);
 #pragma unroll
-        for (int c = 0; c < 64; c += 32) {
+        for (int c = 0; c < kL2N; c += 32) {
             float r[32];
             tc::tmem_ld32(row + c, r);
             if (t < T) {
-                float *out = U + (long long)t * kMlpH + o0 + 64 * (w >> 2) + c;
+                float *out = U + (long long)t * kMlpH + o0 + c;
 #pragma unroll
                 for (int q = 0; q < 32; q += 4)
                     *reinterpret_cast<float4 *>(out + q) = make_float4(fmaxf(r[q], 0.0f), fmaxf(r[q + 1], 0.0f),
@@ -295,7 +321,7 @@ cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const
     cudaError_t e = cudaFuncSetAttribute(mlp_layer2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kL2Smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((T + kL2Rows - 1) / kL2Rows), kMlpH / kL2Rows);
+    const dim3 grid((unsigned)((T + kL2M - 1) / kL2M), kMlpH / kL2N);
     mlp_layer2_tc_kernel<<<grid, kTcThreads, kL2Smem, st>>>(zt, T, w2, b2, U, err);
     return cudaGetLastError();
 }
