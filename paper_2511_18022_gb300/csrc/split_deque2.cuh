@@ -27,6 +27,16 @@
 //  - The grid may be smaller than one thread per scenario: a thread then
 //    walks scenarios s, s + G*T, ... (every thread of a block the same
 //    number of times).
+//  - The route-length test of the front and the ring-overflow test of a
+//    push run once per prefetch block, not per position: the front's
+//    position p is the low bits of its key, and fronts only move to later
+//    positions, so no front reaches its length limit inside a block that
+//    starts with every front at least L + 1 - kPrefetch2 positions younger
+//    than the block's last position; a ring that starts a block at most
+//    R - 4 entries full cannot fill inside it (a position pushes once). A
+//    block where some lane of the warp fails either test walks the exact
+//    per-position tests (rare: the mean window is far shorter than L and
+//    the deque far shorter than the ring).
 //
 // Set-aside scenarios (ring too small, a demand above Q, a negative demand)
 // go to the warp kernel exactly as before.
@@ -44,7 +54,6 @@ namespace cvrpsd {
 struct Deque2 {
     int fg;          // front entry: g
     int fx;          // front key K * (P(p) + Q) + p
-    int fe;          // front expiry step p + L + 1 (LCAP)
     int bg;          // back entry: g
     uint32_t h;      // byte offset of the front slot in the block's rings
     uint32_t b;      // byte offset of the back slot
@@ -62,10 +71,18 @@ __device__ __forceinline__ bool key_expired(int x, uint32_t pk)
     return (int)((uint32_t)x - pk) < 0;
 }
 
+// Whether the front of key x has passed its route-length limit at position
+// i (its position p = x mod K, limit p + L + 1).
+__device__ __forceinline__ bool front_too_long(int x, int i, uint32_t K, int L)
+{
+    return i >= (int)((uint32_t)x & (K - 1u)) + L + 1;
+}
+
 // One position. PUSH: candidate i enters (positions 1..n-1); the last
 // position only reads the window minimum. GENERAL: some C_i <= 0 in this
-// block, so back pops may empty the deque (see split_deque.cuh).
-template <int R, int T, bool LCAP, bool NOWRAP, bool CLAMP, bool PUSH, bool GENERAL>
+// block, so back pops may empty the deque (see split_deque.cuh). LTEST: test
+// the front's route-length limit; OVF: test the push for ring overflow.
+template <int R, int T, bool LTEST, bool OVF, bool NOWRAP, bool CLAMP, bool PUSH, bool GENERAL>
 __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, uint32_t K, uint32_t xi, int L, int Q,
                                         uint32_t rs, bool noback)
 {
@@ -76,7 +93,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         q = min(q, (uint32_t)Q);
     }
     d.pk += q * K;
-    bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe);
+    bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LTEST && front_too_long(d.fx, i, K, L));
     pf = pf & !d.frozen;
     // Front pops. Reaching the back entry with it expired means a demand
     // above Q (only possible without CLAMP): the scenario is bad, frozen
@@ -92,8 +109,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         d.h = pf ? nh : d.h;
         d.fg = pf ? e.x : d.fg;
         d.fx = pf ? e.y : d.fx;
-        if (LCAP) d.fe = pf ? (int)((uint32_t)e.y & (K - 1)) + L + 1 : d.fe;
-        pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LCAP && i >= d.fe));
+        pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LTEST && front_too_long(d.fx, i, K, L)));
     }
     const int gi = d.fg + ci;
     if (!PUSH) return gi;
@@ -110,7 +126,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
             }
         }
         d.b = (d.b + kStride) & kMask;
-        d.frozen |= d.b == d.h;                     // the ring already held R entries
+        if (OVF) d.frozen |= d.b == d.h;            // the ring already held R entries
     } else {
         bool pb = (d.bg >= gi) & !d.frozen;
         bool empty = false;
@@ -128,8 +144,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
             d.h = d.b;
             d.fg = gi;
             d.fx = x;
-            if (LCAP) d.fe = i + L + 1;
-        } else {
+        } else if (OVF) {
             d.frozen |= d.b == d.h;
         }
     }
@@ -153,7 +168,7 @@ __device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<C
 }
 
 // Positions i0 .. i0 + kPrefetch2 - 1 (GUARD: the block may reach past n).
-template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
+template <typename DT, int R, int T, bool LTEST, bool OVF, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
 __device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
 {
@@ -167,9 +182,9 @@ __device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPref
         const bool noback = (e.x & kTab2NoBack) != 0;
         const uint32_t xi = QK + (uint32_t)i;
         if (!GUARD || i < n)
-            dq2_step<R, T, LCAP, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
+            dq2_step<R, T, LTEST, OVF, NOWRAP, CLAMP, true, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
         else
-            out = dq2_step<R, T, LCAP, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
+            out = dq2_step<R, T, LTEST, OVF, NOWRAP, CLAMP, false, GENERAL>(d, q[u], i, ci, K, xi, L, Q, rs, noback);
     }
 }
 
@@ -177,11 +192,29 @@ template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP
 __device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
 {
+    constexpr uint32_t kStride = T * 8u;
+    constexpr uint32_t kMask = R * T * 8u - 1u;
+    // Rings of 16 or more: the overflow test moves to the block; smaller
+    // rings test every push.
+    constexpr bool kBlockOvf = R >= 16;
     const int m = (i0 - 1) / kPrefetch2;
-    if ((tab.nonpos[m >> 5] >> (m & 31)) & 1u)
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
-    else
-        walk2_steps<DT, R, T, LCAP, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+    const bool general = (tab.nonpos[m >> 5] >> (m & 31)) & 1u;
+    bool risk = false;
+    if (LCAP) risk = (int)((uint32_t)d.fx & (K - 1u)) + L < i0 + kPrefetch2 - 1;
+    if (kBlockOvf) risk |= ((d.b - d.h) & kMask) > (uint32_t)(R - 5) * kStride;
+    risk = risk & !d.frozen;                     // a frozen lane no longer pops
+    const bool exact = (LCAP || kBlockOvf) && __any_sync(0xffffffffu, risk);
+    if (exact) {
+        if (general)
+            walk2_steps<DT, R, T, LCAP, true, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+        else
+            walk2_steps<DT, R, T, LCAP, true, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+    } else {
+        if (general)
+            walk2_steps<DT, R, T, false, !kBlockOvf, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+        else
+            walk2_steps<DT, R, T, false, !kBlockOvf, NOWRAP, GUARD, false>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
+    }
 }
 
 template <typename DT, bool CLAMPI, int CAP>
@@ -208,7 +241,6 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     d.h = d.b = slot0;
     d.fg = d.bg = p.g0;
     d.fx = (int)QK;                 // x(0) = K * (0 + Q) + 0
-    d.fe = L + 1;
     d.pk = 0;
     d.qmax = 0;
     d.frozen = false;
