@@ -17,7 +17,9 @@
 //  - When n * Q * K + (Q + 1) * K + n < 2^31 (checked on the host), keys
 //    never wrap and the capacity test is one signed compare (NOWRAP).
 //  - A frozen scenario (ring overflow or a bad demand) only sets a flag that
-//    the front and back tests carry.
+//    the front and back tests carry; with rings of 16 or more and keys that
+//    cannot wrap, freezing instead leaves a one-entry deque whose front
+//    never expires, and the tests carry no flag (fold_frozen).
 //  - Where C_{i-1} > 0 and C_i > C_{i-1}, no scenario can pop the deque's
 //    back at position i (dq2_step gives the argument); the host marks those
 //    positions and the walk skips the back test and its vote there.
@@ -27,16 +29,16 @@
 //  - The grid may be smaller than one thread per scenario: a thread then
 //    walks scenarios s, s + G*T, ... (every thread of a block the same
 //    number of times).
-//  - The route-length test of the front and the ring-overflow test of a
-//    push run once per prefetch block, not per position: the front's
-//    position p is the low bits of its key, and fronts only move to later
-//    positions, so no front reaches its length limit inside a block that
-//    starts with every front at least L + 1 - kPrefetch2 positions younger
-//    than the block's last position; a ring that starts a block at most
-//    R - 4 entries full cannot fill inside it (a position pushes once). A
-//    block where some lane of the warp fails either test walks the exact
-//    per-position tests (rare: the mean window is far shorter than L and
-//    the deque far shorter than the ring).
+//  - The route-length test of the front and (rings of 16 or more) the
+//    ring-overflow test of a push run once per span of two prefetch blocks
+//    (8 positions), not per position: the front's position p is the low
+//    bits of its key, and fronts only move to later positions, so no front
+//    reaches its length limit inside a span that starts with every front
+//    younger than L + 1 - 8 positions before the span's last position; a
+//    ring that starts a span at most R - 8 entries full cannot fill inside
+//    it (a position pushes once). A span where some lane of the warp fails
+//    either test walks the exact per-position tests (rare: the mean window
+//    is far shorter than L and the deque far shorter than the ring).
 //
 // Set-aside scenarios (ring too small, a demand above Q, a negative demand)
 // go to the warp kernel exactly as before.
@@ -78,6 +80,20 @@ __device__ __forceinline__ bool front_too_long(int x, int i, uint32_t K, int L)
     return i >= (int)((uint32_t)x & (K - 1u)) + L + 1;
 }
 
+// Rings of 16 or more: the overflow test moves to the block; smaller rings
+// test every push.
+template <int R> __host__ __device__ constexpr bool block_ovf() { return R >= 16; }
+
+// Frozen lanes folded into the keys (keys that cannot wrap, rings of 16 or
+// more): freezing leaves a consistent one-entry deque whose front key never
+// expires (kNeverExpires > K * P(i) for every i), so the front and back tests
+// need no frozen flag. A ring overflow keeps the entry just pushed as that
+// front (its slot is the one the push overwrote). Back pops stop at such a
+// front as at any other, and GENERAL blocks may still empty the deque and
+// restart it from a real key: the block tests then cover that lane again.
+template <int R, bool NOWRAP> __host__ __device__ constexpr bool fold_frozen() { return NOWRAP && block_ovf<R>(); }
+constexpr int kNeverExpires = 0x7fffffff;
+
 // One position. PUSH: candidate i enters (positions 1..n-1); the last
 // position only reads the window minimum. GENERAL: some C_i <= 0 in this
 // block, so back pops may empty the deque (see split_deque.cuh). LTEST: test
@@ -94,7 +110,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     }
     d.pk += q * K;
     bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LTEST && front_too_long(d.fx, i, K, L));
-    pf = pf & !d.frozen;
+    if (!fold_frozen<R, NOWRAP>()) pf = pf & !d.frozen;
     // Front pops. Reaching the back entry with it expired means a demand
     // above Q (only possible without CLAMP): the scenario is bad, frozen
     // with a front that never expires.
@@ -105,6 +121,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         if (!CLAMP && last && pf) {
             d.frozen = true;
             pf = false;
+            if (fold_frozen<R, NOWRAP>()) d.fx = kNeverExpires;
         }
         d.h = pf ? nh : d.h;
         d.fg = pf ? e.x : d.fg;
@@ -114,9 +131,10 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     const int gi = d.fg + ci;
     if (!PUSH) return gi;
     const int x = (int)(d.pk + xi);       // K * (P(i) + Q) + i
+    constexpr bool kFold = fold_frozen<R, NOWRAP>();
     if (!GENERAL) {
         if (!noback) {
-            bool pb = (d.bg >= gi) & !d.frozen;
+            bool pb = (d.bg >= gi) & (kFold || !d.frozen);
             while (__any_sync(0xffffffffu, pb)) {
                 const uint32_t bp = (d.b - kStride) & kMask;
                 const int below = lds1(rs + bp);
@@ -126,9 +144,13 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
             }
         }
         d.b = (d.b + kStride) & kMask;
-        if (OVF) d.frozen |= d.b == d.h;            // the ring already held R entries
+        if (OVF) {
+            const bool ovf = d.b == d.h;            // the ring already held R entries
+            d.frozen |= ovf;
+            if (kFold && ovf) d.fg = gi, d.fx = kNeverExpires;
+        }
     } else {
-        bool pb = (d.bg >= gi) & !d.frozen;
+        bool pb = (d.bg >= gi) & (kFold || !d.frozen);
         bool empty = false;
         while (__any_sync(0xffffffffu, pb)) {
             const bool emp = d.b == d.h;
@@ -145,7 +167,9 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
             d.fg = gi;
             d.fx = x;
         } else if (OVF) {
-            d.frozen |= d.b == d.h;
+            const bool ovf = d.b == d.h;
+            d.frozen |= ovf;
+            if (kFold && ovf) d.fg = gi, d.fx = kNeverExpires;
         }
     }
     sts2(rs + d.b, gi, x);
@@ -188,22 +212,30 @@ __device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPref
     }
 }
 
-template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
-__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
-                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
+// Whether some lane of the warp needs the exact per-position tests in the
+// SPAN positions from i0: its front may reach the route-length limit, or its
+// ring may fill.
+template <int R, int T, bool LCAP, bool NOWRAP, int SPAN>
+__device__ __forceinline__ bool walk2_exact(const Deque2 &d, int i0, uint32_t K, int L)
 {
     constexpr uint32_t kStride = T * 8u;
     constexpr uint32_t kMask = R * T * 8u - 1u;
-    // Rings of 16 or more: the overflow test moves to the block; smaller
-    // rings test every push.
-    constexpr bool kBlockOvf = R >= 16;
+    if (!LCAP && !block_ovf<R>()) return false;
+    bool risk = false;
+    if (LCAP) risk = (int)((uint32_t)d.fx & (K - 1u)) + L < i0 + SPAN - 1;
+    if (block_ovf<R>()) risk |= ((d.b - d.h) & kMask) > (uint32_t)(R - SPAN - 1) * kStride;
+    if (!fold_frozen<R, NOWRAP>()) risk = risk & !d.frozen;   // a frozen lane no longer pops
+    return __any_sync(0xffffffffu, risk);
+}
+
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
+__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
+                                            int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
+                                            bool exact, int &out)
+{
+    constexpr bool kBlockOvf = block_ovf<R>();
     const int m = (i0 - 1) / kPrefetch2;
     const bool general = (tab.nonpos[m >> 5] >> (m & 31)) & 1u;
-    bool risk = false;
-    if (LCAP) risk = (int)((uint32_t)d.fx & (K - 1u)) + L < i0 + kPrefetch2 - 1;
-    if (kBlockOvf) risk |= ((d.b - d.h) & kMask) > (uint32_t)(R - 5) * kStride;
-    risk = risk & !d.frozen;                     // a frozen lane no longer pops
-    const bool exact = (LCAP || kBlockOvf) && __any_sync(0xffffffffu, risk);
     if (exact) {
         if (general)
             walk2_steps<DT, R, T, LCAP, true, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
@@ -251,18 +283,22 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     unsigned long long *status = p.acc + ACC_STATUS;
     prefetch2<DT, true>(base, tab, 1, n, pitch, status, qa);
     int i0 = 1;
+    // One exactness vote covers both prefetch blocks of an iteration.
+    constexpr int kSpan = 2 * kPrefetch2;
     for (; i0 + 3 * kPrefetch2 - 1 < n; i0 += 2 * kPrefetch2) {
         prefetch2<DT, false>(base, tab, i0 + kPrefetch2, n, pitch, status, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        const bool ex = walk2_exact<R, T, LCAP, NOWRAP, kSpan>(d, i0, K, L);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qa, tab, i0, n, K, QK, L, Q, rs, ex, out);
         prefetch2<DT, false>(base, tab, i0 + 2 * kPrefetch2, n, pitch, status, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
+        walk2_block<DT, R, T, LCAP, NOWRAP, false>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, ex, out);
     }
     for (; i0 <= n; i0 += 2 * kPrefetch2) {
         prefetch2<DT, true>(base, tab, i0 + kPrefetch2, n, pitch, status, qb);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, out);
+        const bool ex = walk2_exact<R, T, LCAP, NOWRAP, kSpan>(d, i0, K, L);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qa, tab, i0, n, K, QK, L, Q, rs, ex, out);
         if (i0 + kPrefetch2 > n) break;
         prefetch2<DT, true>(base, tab, i0 + 2 * kPrefetch2, n, pitch, status, qa);
-        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, out);
+        walk2_block<DT, R, T, LCAP, NOWRAP, true>(d, qb, tab, i0 + kPrefetch2, n, K, QK, L, Q, rs, ex, out);
     }
     aside = d.frozen || d.qmax > (uint32_t)Q;
     return out;
@@ -271,13 +307,16 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
 // The walk is compiled for 2048 resident threads per SM (the most an SM
 // holds): 32 registers a thread, and with rings of 8 its blocks fit the
 // shared memory too. Full occupancy measured 4 % faster than the compiler's
-// own choice (40 registers, 12 blocks of 128).
+// own choice (40 registers, 12 blocks of 128). Rings of 16 fit fewer blocks
+// by shared memory (6 of 256 threads), but giving those kernels the 40
+// registers that would allow measured 16 % slower (the compiler then moves
+// table work from the uniform datapath to the vector pipes).
 constexpr int kD2ThreadsPerSM = 2048;
-template <int T>
+template <int R, int T>
 constexpr int d2_min_blocks() { return kD2ThreadsPerSM / T; }
 
 template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
-__global__ void __launch_bounds__(T, d2_min_blocks<T>()) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
+__global__ void __launch_bounds__(T, d2_min_blocks<R, T>()) split_deque2_kernel(const Walk2Params p, const __grid_constant__ TabParam<CAP> tab)
 {
     // Rings [R][T] of (g, key) slots: thread t's slot k is at byte
     // (k * T + t) * 8, so a warp's accesses never conflict.
