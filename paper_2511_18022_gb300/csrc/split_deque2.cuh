@@ -18,8 +18,10 @@
 //    never wrap and the capacity test is one signed compare (NOWRAP).
 //  - A frozen scenario (ring overflow or a bad demand) only sets a flag that
 //    the front and back tests carry; with rings of 16 or more and keys that
-//    cannot wrap, freezing instead leaves a one-entry deque whose front
-//    never expires, and the tests carry no flag (fold_frozen).
+//    cannot wrap, a frozen lane instead keeps walking a consistent deque and
+//    the tests carry no flag (fold_frozen).
+//  - A front walk moves only the front slot and reads only keys; the new
+//    front's (g, key) is read from its slot once the walk ends.
 //  - Where C_{i-1} > 0 and C_i > C_{i-1}, no scenario can pop the deque's
 //    back at position i (dq2_step gives the argument); the host marks those
 //    positions and the walk skips the back test and its vote there.
@@ -84,15 +86,14 @@ __device__ __forceinline__ bool front_too_long(int x, int i, uint32_t K, int L)
 // test every push.
 template <int R> __host__ __device__ constexpr bool block_ovf() { return R >= 16; }
 
-// Frozen lanes folded into the keys (keys that cannot wrap, rings of 16 or
-// more): freezing leaves a consistent one-entry deque whose front key never
-// expires (kNeverExpires > K * P(i) for every i), so the front and back tests
-// need no frozen flag. A ring overflow keeps the entry just pushed as that
-// front (its slot is the one the push overwrote). Back pops stop at such a
-// front as at any other, and GENERAL blocks may still empty the deque and
-// restart it from a real key: the block tests then cover that lane again.
+// Frozen lanes that keep walking (keys that cannot wrap, rings of 16 or
+// more): a frozen lane's result is discarded, so it only has to stay a
+// consistent deque, and then the front and back tests need no frozen flag.
+// A ring overflow restarts the deque from the entry just pushed (its slot is
+// the one the push overwrote); a demand above Q leaves the front on the back
+// entry. Either way every later front walk ends at the back (or freezes
+// there again) and every back walk at the front, as for any other lane.
 template <int R, bool NOWRAP> __host__ __device__ constexpr bool fold_frozen() { return NOWRAP && block_ovf<R>(); }
-constexpr int kNeverExpires = 0x7fffffff;
 
 // One position. PUSH: candidate i enters (positions 1..n-1); the last
 // position only reads the window minimum. GENERAL: some C_i <= 0 in this
@@ -111,22 +112,27 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     d.pk += q * K;
     bool pf = key_expired<NOWRAP>(d.fx, d.pk) | (LTEST && front_too_long(d.fx, i, K, L));
     if (!fold_frozen<R, NOWRAP>()) pf = pf & !d.frozen;
-    // Front pops. Reaching the back entry with it expired means a demand
-    // above Q (only possible without CLAMP): the scenario is bad, frozen
-    // with a front that never expires.
-    while (__any_sync(0xffffffffu, pf)) {
-        const bool last = d.h == d.b;
-        const uint32_t nh = (d.h + kStride) & kMask;
-        const int2 e = lds2(rs + nh);
-        if (!CLAMP && last && pf) {
-            d.frozen = true;
-            pf = false;
-            if (fold_frozen<R, NOWRAP>()) d.fx = kNeverExpires;
-        }
-        d.h = pf ? nh : d.h;
-        d.fg = pf ? e.x : d.fg;
-        d.fx = pf ? e.y : d.fx;
-        pf = pf & (key_expired<NOWRAP>(d.fx, d.pk) | (LTEST && front_too_long(d.fx, i, K, L)));
+    // Front pops. The walk reads only the keys and moves h; the new front's
+    // (g, key) is read once after it. Reaching the back entry with it expired
+    // means a demand above Q (only possible without CLAMP): the scenario is
+    // bad and frozen, its front left on the back entry. The slot at h always
+    // holds the front (a frozen lane's overwritten slot included, which only
+    // that lane reads).
+    if (__any_sync(0xffffffffu, pf)) {
+        do {
+            const bool last = d.h == d.b;
+            const uint32_t nh = (d.h + kStride) & kMask;
+            const int key = lds1(rs + nh + 4u);
+            if (!CLAMP && last && pf) {
+                d.frozen = true;
+                pf = false;
+            }
+            d.h = pf ? nh : d.h;
+            pf = pf & (key_expired<NOWRAP>(key, d.pk) | (LTEST && front_too_long(key, i, K, L)));
+        } while (__any_sync(0xffffffffu, pf));
+        const int2 e = lds2(rs + d.h);
+        d.fg = e.x;
+        d.fx = e.y;
     }
     const int gi = d.fg + ci;
     if (!PUSH) return gi;
@@ -147,7 +153,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         if (OVF) {
             const bool ovf = d.b == d.h;            // the ring already held R entries
             d.frozen |= ovf;
-            if (kFold && ovf) d.fg = gi, d.fx = kNeverExpires;
+            if (kFold && ovf) d.fg = gi, d.fx = x;
         }
     } else {
         bool pb = (d.bg >= gi) & (kFold || !d.frozen);
@@ -169,7 +175,7 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
         } else if (OVF) {
             const bool ovf = d.b == d.h;
             d.frozen |= ovf;
-            if (kFold && ovf) d.fg = gi, d.fx = kNeverExpires;
+            if (kFold && ovf) d.fg = gi, d.fx = x;
         }
     }
     sts2(rs + d.b, gi, x);
