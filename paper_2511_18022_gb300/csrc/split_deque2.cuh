@@ -141,6 +141,17 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     if (!GENERAL) {
         if (!noback) {
             bool pb = (d.bg >= gi) & (kFold || !d.frozen);
+            // Where the back can pop at all (C_i <= C_{i-1} or C_{i-1} <= 0),
+            // nearly every warp pops at least once (lanes whose front did
+            // not move pop the back whenever C_i <= C_{i-1}): the first step
+            // runs without a vote.
+            {
+                const uint32_t bp = (d.b - kStride) & kMask;
+                const int below = lds1(rs + bp);
+                d.b = pb ? bp : d.b;
+                d.bg = pb ? below : d.bg;
+                pb = pb & (below >= gi);
+            }
             while (__any_sync(0xffffffffu, pb)) {
                 const uint32_t bp = (d.b - kStride) & kMask;
                 const int below = lds1(rs + bp);
