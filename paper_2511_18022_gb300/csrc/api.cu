@@ -464,11 +464,11 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
                 if (timed) CK(cudaEventRecord(ctx->ev_t[0], stream), "cudaEventRecord");
                 DequeShape ran{};
                 const int rounds = ctx->cfg.rounds;
-                // untuned default: 256 threads, rings of 16 (rings of 8 run the main kernel
-                // 0.2 % faster at full size but set aside more scenarios, whose warp-kernel
-                // pass costs about 0.17 ms each at n = 1000)
+                // untuned default: 128 threads, rings of 16 (13 blocks fill an SM's
+                // shared memory; rings of 8 need a ring-overflow test on every push
+                // and set aside more scenarios, and measured 20 % slower at n = 1000)
                 const DequeShape want = ctx->cfg.threads ? DequeShape{shape.threads, 1, shape.ring}
-                                                         : DequeShape{256, 1, 16};
+                                                         : DequeShape{128, 1, 16};
                 CK(launch_split_deque2(p, ctx->h_tab, demand_dtype, want, rounds, &ran, stream),
                    "split_deque2 launch");
                 if (timed) CK(cudaEventRecord(ctx->ev_t[1], stream), "cudaEventRecord");
