@@ -447,7 +447,8 @@ def roofline_lines(args, S, n, kernel_ms, st, clk, int_ops, int_ms, relax_per_ce
         roof["issue"] = {"achieved": round(iach / 1e9, 1), "peak": round(ipeak / 1e9, 1),
                          "unit": "G warp-instructions/s", "frac": round(iach / ipeak, 4),
                          "warp_instructions_per_launch": winst,
-                         "counts_shape": shape if shape in t.get("inst_executed", {}) else "256,1,8,walk2",
+                         "counts_shape": shape if shape in t.get("inst_executed", {})
+                         else next(iter(t.get("inst_executed", {})), None),
                          "per_warp_position": round(winst / (S / 32 * n), 2)}
     return roof
 
