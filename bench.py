@@ -571,51 +571,75 @@ def run_surrogate(args):
     scale, mae = search.train_surrogate(sur, tours, costs, dist=inst.dist, epochs=args.epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    start = np.random.default_rng(1234).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
     M, k = 4096, 64
+    trained = sur.state()
+    starts = [np.random.default_rng(1234 + r).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+              for r in range(max(1, args.repeats))]
     # warm-up on a copy (first launches, allocations)
-    search.LocalSearch(sp.ctx, inst, D, start, M=M, seed=1, exact_all=True).run(max(args.warmup, 1))
-    search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=1, scale=scale).run(
+    search.LocalSearch(sp.ctx, inst, D, starts[0], M=M, seed=1, exact_all=True).run(max(args.warmup, 1))
+    search.LocalSearch(sp.ctx, inst, D, starts[0], surrogate=sur, M=M, k=k, seed=1, scale=scale).run(
         max(args.warmup, 1))
-    # plain-Split search: every one of the M neighbours split exactly
-    plain = search.LocalSearch(sp.ctx, inst, D, start, M=M, seed=99, exact_all=True)
-    plog = plain.run(args.steps)
-    # screened search, same moves: equal iterations, then equal wall time
-    screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99,
-                                  retrain_every=25, scale=scale)
-    slog = screened.run(args.steps)
-    timed = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99,
-                               retrain_every=25, scale=scale)
-    tlog = timed.run(1_000_000, seconds=plog.seconds)
+    # Per start: the plain-Split search (every one of the M neighbours split
+    # exactly), then the screened search with the same moves, at equal
+    # iterations and at equal wall time, each from the trained surrogate.
+    # One search is one sample of a noisy trajectory: several starts.
+    runs = []
+    for r, start in enumerate(starts):
+        plain = search.LocalSearch(sp.ctx, inst, D, start, M=M, seed=99 + r, exact_all=True)
+        plog = plain.run(args.steps)
+        sur.load_state(trained)
+        screened = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99 + r,
+                                      retrain_every=25, scale=scale)
+        slog = screened.run(args.steps)
+        sur.load_state(trained)
+        timed = search.LocalSearch(sp.ctx, inst, D, start, surrogate=sur, M=M, k=k, seed=99 + r,
+                                   retrain_every=25, scale=scale)
+        tlog = timed.run(1_000_000, seconds=plog.seconds)
+        runs.append({"start": r, "plain_cost": plain.cur_cost, "plain_seconds": plog.seconds,
+                     "plain_candidates_per_s": plog.candidates_per_s,
+                     "screened_cost": screened.cur_cost, "screened_seconds": slog.seconds,
+                     "screened_candidates_per_s": slog.candidates_per_s,
+                     "gap_equal_iterations": (screened.cur_cost - plain.cur_cost) / plain.cur_cost,
+                     "timed_cost": timed.cur_cost, "timed_iterations": timed.iterations,
+                     "gap_equal_time": (timed.cur_cost - plain.cur_cost) / plain.cur_cost,
+                     "plain_tour": plain.cur.cpu().numpy(), "screened_tour": screened.cur.cpu().numpy()})
+    sur.load_state(trained)
     # the old baseline: k random neighbours split exactly
-    rand = search.LocalSearch(sp.ctx, inst, D, start, k=k, seed=99)
+    rand = search.LocalSearch(sp.ctx, inst, D, starts[0], k=k, seed=99)
     rlog = rand.run(args.steps)
     quality = [search.neighbourhood_quality(sp.ctx, inst, D, sur, scale, t, M=M, k=k, seed=17 + j)
-               for j, t in enumerate([start, plain.cur.cpu().numpy(), screened.cur.cpu().numpy()])]
+               for j, t in enumerate([starts[0], runs[0]["plain_tour"], runs[0]["screened_tour"]])]
     if rank == 0:
-        gap_it = (screened.cur_cost - plain.cur_cost) / plain.cur_cost
-        gap_t = (timed.cur_cost - plain.cur_cost) / plain.cur_cost
+        cand_s = float(np.mean([x["screened_candidates_per_s"] for x in runs]))
+        plain_cand_s = float(np.mean([x["plain_candidates_per_s"] for x in runs]))
+        s_ms = float(np.mean([x["screened_seconds"] for x in runs])) / args.steps * 1e3
+        p_ms = float(np.mean([x["plain_seconds"] for x in runs])) / args.steps * 1e3
         print(json.dumps({
             "metric": "surrogate-screened local search: candidate tours/s (exact Split on the top 64 of 4096)",
-            "value": slog.candidates_per_s, "unit": "tours/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": slog.seconds / args.steps * 1e3, "higher_is_better": True,
+            "value": cand_s, "unit": "tours/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, fp32 accumulation; i32 Split",
             "data": "synthetic",
             "config": {"workload": w.name, "n": inst.n, "S": S, "Q": inst.Q, "L": inst.L,
                        "train_pairs": args.train_pairs, "epochs": args.epochs, "screen": M, "exact": k},
             "plain_split_search": {"what": f"all {M} neighbours split exactly per iteration, same moves",
-                                   "candidate_tours_per_s": plog.candidates_per_s,
-                                   "final_saa_cost": plain.cur_cost, "iterations": args.steps,
-                                   "ms_per_iteration": plog.seconds / args.steps * 1e3},
-            "screened_equal_iterations": {"final_saa_cost": screened.cur_cost, "iterations": args.steps,
-                                          "gap_vs_plain": gap_it,
-                                          "ms_per_iteration": slog.seconds / args.steps * 1e3},
-            "screened_equal_time": {"final_saa_cost": timed.cur_cost, "iterations": timed.iterations,
-                                    "seconds": tlog.seconds, "gap_vs_plain": gap_t},
-            "random_k_search": {"what": f"{k} random neighbours split exactly per iteration",
+                                   "candidate_tours_per_s": plain_cand_s, "iterations": args.steps,
+                                   "ms_per_iteration": p_ms,
+                                   "final_saa_cost": [x["plain_cost"] for x in runs]},
+            "screened_equal_iterations": {"final_saa_cost": [x["screened_cost"] for x in runs],
+                                          "iterations": args.steps, "ms_per_iteration": s_ms,
+                                          "gap_vs_plain": [x["gap_equal_iterations"] for x in runs],
+                                          "mean_gap_vs_plain": float(np.mean([x["gap_equal_iterations"]
+                                                                              for x in runs]))},
+            "screened_equal_time": {"final_saa_cost": [x["timed_cost"] for x in runs],
+                                    "iterations": [x["timed_iterations"] for x in runs],
+                                    "gap_vs_plain": [x["gap_equal_time"] for x in runs],
+                                    "mean_gap_vs_plain": float(np.mean([x["gap_equal_time"] for x in runs]))},
+            "starts": len(runs),
+            "random_k_search": {"what": f"{k} random neighbours split exactly per iteration (first start)",
                                 "final_saa_cost": rand.cur_cost,
                                 "ms_per_iteration": rlog.seconds / args.steps * 1e3},
-            "speedup_candidates": slog.candidates_per_s / plog.candidates_per_s,
+            "speedup_candidates": cand_s / plain_cand_s,
             "surrogate": {"holdout_mae": mae, "training_cost_sd": float(costs.std().item()),
                           "label_seconds": t_label, "train_seconds": t_train,
                           "neighbourhoods": quality,
@@ -747,7 +771,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default shape)")
     ap.add_argument("--train-pairs", type=int, default=200_000, help="surrogate-n200: labelled tours")
     ap.add_argument("--epochs", type=int, default=8, help="surrogate-n200: training epochs")
-    ap.add_argument("--repeats", type=int, default=3, help="oos-n200: searches per training-set size")
+    ap.add_argument("--repeats", type=int, default=3, help="oos-n200: searches per training-set size; "
+                    "surrogate-n200: search starts")
     args = ap.parse_args()
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")

@@ -7,7 +7,9 @@ the exact Split evaluates them.
 
 Network (width H = 256), for a tour sigma_1..sigma_n of an instance with
 customer features (x, y, mean demand mu, demand sd), capacity Q and distances c
-(with bf16=True the weights and phi are rounded to bfloat16 first):
+(with bf16=True the weights are rounded to bfloat16 first and each feature
+is carried as a bfloat16 pair, hi = bf16(v) plus lo = bf16(v - hi), v the
+feature in float32):
     phi_k = (x/1000, y/1000, mu/Q, sd/Q, frac(sum_{t<=k} mu_{sigma_t} / Q))
     h_k   = relu(W1 phi_k + b1)
     z     = (1/n) sum_k h_k
@@ -49,6 +51,14 @@ def to_bf16(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def to_bf16_pair(x):
+    """hi + lo with hi = bf16(v), lo = bf16(v - hi), v = float32(x): the two
+    bfloat16 numbers a feature is carried as (about 16 significant bits)."""
+    v = np.asarray(x, dtype=np.float32).astype(np.float64)
+    hi = to_bf16(v)
+    return hi + to_bf16(v - hi)
+
+
 def features(tours, cust, dist, Q, len_mean=0.0, len_sd=None):
     """phi [T][n][5] and t [T] for tours [T][n] (customer ids 1..n)."""
     tours = np.asarray(tours, dtype=np.int64)
@@ -65,13 +75,14 @@ def features(tours, cust, dist, Q, len_mean=0.0, len_sd=None):
 
 def forward(p, phi, t, bf16=False):
     """Network outputs and the intermediates the backward pass needs. With
-    bf16 the weights and the per-position features are rounded to bfloat16
-    first (the library's operands); everything else stays float64."""
+    bf16 the weights are rounded to bfloat16 and the per-position features
+    replaced by their bfloat16 pairs (the library's operands); everything else
+    stays float64."""
     W1, b1, W2, b2, w3, b3 = unpack(p)
     if bf16:
         W1, b1, W2, b2, w3 = (to_bf16(a) for a in (W1, b1, W2, b2, w3))
         b3 = to_bf16(np.array([b3]))[0]
-        phi = to_bf16(phi)
+        phi = to_bf16_pair(phi)
     pre = np.einsum("tkf,jf->tkj", phi, W1) + b1          # [T][n][H]
     z = np.maximum(pre, 0.0).mean(axis=1)                # [T][H]
     zt = np.concatenate([z, t[:, None]], axis=1)          # [T][H+1]
@@ -84,7 +95,7 @@ def forward(p, phi, t, bf16=False):
 def loss_and_grad(p, phi, t, target, bf16=False):
     y, c = forward(p, phi, t, bf16)
     if bf16:
-        phi = to_bf16(phi)
+        phi = to_bf16_pair(phi)
     T, n, _ = phi.shape
     err = y - np.asarray(target, dtype=np.float64)
     loss = float((err ** 2).mean())

@@ -1,6 +1,6 @@
 // Surrogate network for screening local-search neighbours: training and
-// inference kernels. BF16 weights and per-position features, FP32
-// activations and accumulation. Layer 1's forward pass runs on the tensor
+// inference kernels. BF16 weights, per-position features as BF16 hi + lo
+// pairs (about 16 significant bits), FP32 activations and accumulation. Layer 1's forward pass runs on the tensor
 // cores (mlp_tc.cu); this file holds the rest: the backward pass of layer 1
 // (which recomputes the pre-activations from the same BF16 operands), the
 // layer 2 products, the output layer, the loss and Adam.
@@ -68,13 +68,16 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
             for (int q = 0; q < w; ++q) off += s_part[q];
             const float cum = off + v;
             if (k < n) {
-                // features in BF16, as the tensor-core forward pass takes them
+                // features as the tensor-core forward pass takes them: the sum
+                // of a BF16 pair hi = bf16(v), lo = bf16(v - hi)
+                const float v[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
+                                          a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
                 float *f = feat + 5 * k;
-                f[0] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 0]));
-                f[1] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 1]));
-                f[2] = __bfloat162float(__float2bfloat16_rn(m));
-                f[3] = __bfloat162float(__float2bfloat16_rn(a.cust[(c - 1) * 4 + 3]));
-                f[4] = __bfloat162float(__float2bfloat16_rn(cum - floorf(cum)));
+#pragma unroll
+                for (int q = 0; q < kMlpIn1; ++q) {
+                    const float hi = __bfloat162float(__float2bfloat16_rn(v[q]));
+                    f[q] = hi + __bfloat162float(__float2bfloat16_rn(v[q] - hi));
+                }
             }
             __syncthreads();
             if (j == kMlpH - 1) s_carry = cum;

@@ -3,9 +3,12 @@
 //
 // Per tour the layer is a small matrix product: the pre-activations of the
 // H = 256 hidden units at the n positions are W1' (H x 16) times F' (16 x n),
-// where F' holds the five per-position features, a constant 1 (so that the
-// bias b1 rides in W1' as a sixth column) and zero padding to K = 16, one MMA
-// step of kind::f16 with BF16 operands. The accumulators land in tensor
+// one MMA step of kind::f16 with BF16 operands. F' holds each of the five
+// per-position features as two BF16 numbers, hi = bf16(v) in columns 0-4 and
+// lo = bf16(v - hi) in columns 6-10, with a constant 1 in column 5; W1' holds
+// W1 in columns 0-4 and again in 6-10, and the bias b1 in column 5. So the
+// product keeps about 16 significant bits of the features against the exact
+// BF16 weights, at no extra MMA: K = 16 has room. The accumulators land in tensor
 // memory as FP32, hidden units on the 128 TMEM lanes and positions on the
 // columns, so the mean-pooling over positions is a sum along each thread's
 // own row: ReLU and sum in registers, no cross-thread reduction.
@@ -60,12 +63,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
     const uint32_t f_s = (uint32_t)__cvta_generic_to_shared(s_f);
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
 
-    // W1' = [W1 | b1 | 0]: row h, columns 0..4 weights, 5 bias, 6..15 zero.
+    // W1' = [W1 | b1 | W1 | 0]: row h, columns 0..4 and 6..10 weights, 5 bias,
+    // 11..15 zero.
     for (int e = j; e < kMlpH * kTcK; e += kTcThreads) {
         const int h = e / kTcK, k = e % kTcK;
         __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
         if (k < kMlpIn1) v = a.w1[h * kMlpIn1 + k];
         else if (k == kMlpIn1) v = a.b1[h];
+        else if (k < 2 * kMlpIn1 + 1) v = a.w1[h * kMlpIn1 + k - kMlpIn1 - 1];
         *reinterpret_cast<__nv_bfloat16 *>(s_w1 + tc::kmajor_offset(h, k, 2)) = v;
     }
     if (j == 0) {
@@ -119,12 +124,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_tc_kernel(MlpLayer1A
 #pragma unroll
             for (int q = 0; q < kTcK; ++q) f[q] = zero;
             if (k < n) {
-                f[0] = __float2bfloat16_rn(a.cust[(c - 1) * 4 + 0]);
-                f[1] = __float2bfloat16_rn(a.cust[(c - 1) * 4 + 1]);
-                f[2] = __float2bfloat16_rn(m);
-                f[3] = __float2bfloat16_rn(a.cust[(c - 1) * 4 + 3]);
-                f[4] = __float2bfloat16_rn(cum - floorf(cum));
-                f[5] = one;
+                const float v[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
+                                          a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
+#pragma unroll
+                for (int q = 0; q < kMlpIn1; ++q) {
+                    f[q] = __float2bfloat16_rn(v[q]);
+                    f[q + kMlpIn1 + 1] = __float2bfloat16_rn(v[q] - __bfloat162float(f[q]));
+                }
+                f[kMlpIn1] = one;
             }
             // row j of F': two 16-byte halves (k 0..7 and 8..15)
 #pragma unroll

@@ -81,11 +81,14 @@ class LocalSearch:
 
     def __init__(self, ctx, inst, D, start, *, surrogate: Surrogate | None = None, M: int = 4096, k: int = 64,
                  seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4,
-                 moves_block: int = 64, exact_all: bool = False):
+                 moves_block: int = 64, exact_all: bool = False, explore: int = 0):
         """Three modes: with a surrogate, screen M neighbours and split the k
         best exactly; with exact_all, split all M neighbours exactly (the
         plain-Split search the screened one is measured against: same moves
-        for the same seed); otherwise split k random neighbours."""
+        for the same seed); otherwise split k random neighbours. `explore`
+        (screened mode) gives that many of the k exact evaluations to
+        neighbours the surrogate did not pick: the last `explore` of the
+        iteration's random moves."""
         import torch
         self.ctx, self.inst, self.D = ctx, inst, D
         self.n = inst.n
@@ -95,6 +98,9 @@ class LocalSearch:
         self.M = M if (surrogate is not None or exact_all) else k
         k = self.M if exact_all else k
         self.k = k
+        if not 0 <= explore < k or (explore and surrogate is None):
+            raise ValueError("explore needs a surrogate and 0 <= explore < k")
+        self.explore = explore
         self.sur = surrogate
         self.rng = np.random.default_rng(seed)
         self.eval = Evaluator(ctx, inst, D)
@@ -140,8 +146,11 @@ class LocalSearch:
         cvrpsd_neighbors(self.ctx, self.cur, self._next_moves(), self.cand)
         if self.sur is not None:
             self.sur.predict(self.cand, self.scores)
-            cvrpsd_topk(self.ctx, self.scores, self.k, self.idx)
-            cvrpsd_gather_tours(self.ctx, self.cand, self.idx, self.top)
+            kt = self.k - self.explore
+            cvrpsd_topk(self.ctx, self.scores, kt, self.idx)
+            cvrpsd_gather_tours(self.ctx, self.cand, self.idx[:kt], self.top)
+            if self.explore:
+                self.top[kt:].copy_(self.cand[self.M - self.explore:])
             chosen = self.top
         elif self.exact_all:
             chosen = self.cand

@@ -56,3 +56,22 @@ def test_bf16_rounding():
     assert abs(r[3] + 3.140625) < 1e-12
     bits = r.astype(np.float32).view(np.uint32)
     assert (bits & 0xFFFF == 0).all()
+
+
+def test_bf16_pair():
+    """A feature carried as two bfloat16 numbers: exact for values of at most
+    16 significant bits, within 2^-16 relative otherwise, and both parts are
+    bfloat16 bit patterns."""
+    exact = np.array([1.0 + 2.0 ** -12, 0.75 + 2.0 ** -15, -(3.0 + 2.0 ** -10)], dtype=np.float32)
+    assert np.array_equal(M.to_bf16_pair(exact), exact.astype(np.float64))
+    rng = np.random.default_rng(5)
+    v = rng.uniform(-2.0, 2.0, 1000).astype(np.float32)
+    pair = M.to_bf16_pair(v)
+    assert np.all(np.abs(pair - v) <= np.abs(v) * 2.0 ** -16)
+    # one bfloat16 alone is off by up to 2^-9 relative; the pair is far closer
+    assert np.abs(M.to_bf16(v) - v).max() > 100 * np.abs(pair - v).max()
+    hi = M.to_bf16(v)
+    lo = M.to_bf16(v.astype(np.float64) - hi)
+    for part in (hi, lo):
+        assert (part.astype(np.float32).view(np.uint32) & 0xFFFF == 0).all()
+    assert np.array_equal(hi + lo, pair)

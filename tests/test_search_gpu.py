@@ -324,3 +324,29 @@ def test_screened_search_against_plain_split_search(sp, cv):
     q = search.neighbourhood_quality(sp.ctx, inst, D, sur, scale, screened.cur.cpu().numpy(), M=2048, k=32)
     assert q["spearman"] > 0.3
     sur.close()
+
+
+def test_screened_search_exploration_slots(sp, cv):
+    """With `explore` slots the k exact evaluations are the k - explore best
+    by the surrogate plus the iteration's last `explore` random neighbours:
+    the cost trace stays non-increasing, the reported cost is the exact cost
+    of the final tour, and bad settings are refused."""
+    from paper_2511_18022_gb300 import search
+    inst = make_instance(60, 1, 10, seed=13, Q=40, L=15)
+    S = 257
+    D = demand_matrix(inst.mu, inst.region, 1, 5, S, dtype=np.int16)
+    dD = torch.from_numpy(D).cuda()
+    cust = search.customer_features(inst, D)
+    sur = cv.Surrogate(sp.ctx, cust, inst.dist, Q=float(inst.Q), seed=3)
+    start = np.random.default_rng(2).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
+    with pytest.raises(ValueError):
+        search.LocalSearch(sp.ctx, inst, dD, start, surrogate=sur, M=256, k=16, explore=16)
+    with pytest.raises(ValueError):
+        search.LocalSearch(sp.ctx, inst, dD, start, k=16, explore=4)
+    ls = search.LocalSearch(sp.ctx, inst, dD, start, surrogate=sur, M=256, k=16, seed=4, explore=4)
+    log = ls.run(80)
+    assert all(b <= a for a, b in zip(log.costs, log.costs[1:]))
+    _, s, inf, _ = oracle.split_costs(ls.cur.cpu().numpy(), inst.dist, D, inst.Q, inst.L)
+    assert ls.cur_cost == s / (S - inf)
+    assert sorted(ls.cur.cpu().tolist()) == list(range(1, inst.n + 1))
+    sur.close()
