@@ -138,7 +138,10 @@ __device__ __forceinline__ int dq2_step(Deque2 &d, uint32_t q, int i, int ci, ui
     if (!PUSH) return gi;
     const int x = (int)(d.pk + xi);       // K * (P(i) + Q) + i
     constexpr bool kFold = fold_frozen<R, NOWRAP>();
-    if (!GENERAL) {
+    // In a GENERAL block only the positions with C_i <= 0 need the back walk
+    // that may empty the deque: with C_i > 0 the new value exceeds the
+    // front's, so the back walk stops there as in any other block.
+    if (!GENERAL || ci > 0) {
         if (!noback) {
             bool pb = (d.bg >= gi) & (kFold || !d.frozen);
             // Where the back can pop at all (C_i <= C_{i-1} or C_{i-1} <= 0),
