@@ -45,7 +45,10 @@ KERNEL_FILES = ["paper_2511_18022_gb300/csrc/split_deque.cuh",
                 "paper_2511_18022_gb300/csrc/kernels.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_deque_million-n1000.traffic.json")
 BATCH_KERNEL_FILES = ["paper_2511_18022_gb300/csrc/split_batch.cu",
+                      "paper_2511_18022_gb300/csrc/split_batch2.cu",
                       "paper_2511_18022_gb300/csrc/split_deque.cuh",
+                      "paper_2511_18022_gb300/csrc/split_deque2.cuh",
+                      "paper_2511_18022_gb300/csrc/deque2.h",
                       "paper_2511_18022_gb300/csrc/kernels.h"]
 BATCH_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_batch_batched-512.traffic.json")
 

@@ -27,6 +27,8 @@ UNITS = [("split_deque.cu", [f"-DCVRPSD_DEQUE_PART={k}"], f"split_deque_{k}.o") 
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=1"], "split_batch_1.o"),
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=2"], "split_batch_2.o"),
     ("split_batch.cu", ["-DCVRPSD_BATCH_PART=3"], "split_batch_3.o"),
+    ("split_batch2.cu", ["-DCVRPSD_BATCH2_PART=0"], "split_batch2_0.o"),
+    ("split_batch2.cu", ["-DCVRPSD_BATCH2_PART=1"], "split_batch2_1.o"),
     ("split_warp.cu", [], "split_warp.o"),
     ("gen_demand.cu", [], "gen_demand.o"),
     ("api.cu", [], "api.o"),

@@ -943,6 +943,8 @@ int cvrpsd_batch_create(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *tour
     bp.list = b->d_list;
     bp.list_cap = list_cap;
     bp.max_n = max_n;
+    bp.walk2 = demand_dtype == CVRPSD_I16;
+    for (int t = 0; t < T; ++t) bp.walk2 &= batch2_keys_fit(hd[t].n, hd[t].Q, hd[t].K);
     int per_sm = 0;
     BK(launch_split_batch(bp, demand_dtype, lcap, shape, 0, true, &per_sm, nullptr), "configure batch kernel");
     if (per_sm < 1) per_sm = 1;

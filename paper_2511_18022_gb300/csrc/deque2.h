@@ -32,6 +32,17 @@ template <int CAP>
 struct TabParam {
     uint2 e[CAP];
     uint32_t nonpos[(CAP / kPrefetch2 + 31) / 32];
+    static constexpr int kCap = CAP;
+#ifdef __CUDACC__
+    // The walk's view of a table (see TabShared2 for the batch kernel's).
+    __device__ __forceinline__ uint2 entry(int i) const { return e[i - 1]; }
+    __device__ __forceinline__ uint32_t row(int i) const { return e[i - 1].x & kTab2RowMask; }
+    __device__ __forceinline__ bool general(int i0) const
+    {
+        const int m = (i0 - 1) / kPrefetch2;
+        return (nonpos[m >> 5] >> (m & 31)) & 1u;
+    }
+#endif
 };
 
 struct Walk2Params {
@@ -44,6 +55,7 @@ struct Walk2Params {
     int32_t *out_cost;         // device [S] or nullptr
     unsigned long long *acc;   // device [ACC_WORDS]
     int32_t *ovf_list;         // device [S]
+    unsigned long long *status;   // device word for index-check status bits
 };
 
 // Whether the second walk can run this Split (otherwise the first walk runs):

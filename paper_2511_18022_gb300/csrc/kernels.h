@@ -120,6 +120,8 @@ struct BatchParams {
     int2 *list;                   // device [list_cap]: set-aside (tour, scenario)
     long long list_cap;
     int max_n;                    // largest tour
+    int walk2;                    // int16 demands and keys that cannot wrap in every tour: the
+                                  // second walk runs the one-scenario-per-thread shapes
 };
 
 // Dynamic shared memory of the batch kernel: rings, then the current tour's table.
@@ -132,6 +134,20 @@ inline size_t split_batch_smem(int max_n, const DequeShape &shape)
 // reports blocks per SM in *blocks_per_sm.
 cudaError_t launch_split_batch(const BatchParams &b, int esize, bool lcap, const DequeShape &shape, int grid,
                                bool configure_only, int *blocks_per_sm, cudaStream_t stream);
+// The batch kernel on the second walk (split_batch2.cu), which
+// launch_split_batch picks where b.walk2 is set and the shape has one
+// scenario per thread.
+bool batch2_shape_compiled(const DequeShape &s);
+cudaError_t launch_split_batch2_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                    int *blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_split_batch2_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
+                                      int *blocks_per_sm, cudaStream_t stream);
+// Whether every key K (P + Q) + p of an int16 walk stays below 2^31 (demands
+// read unclamped: one bad demand may add up to 65535 before the walk freezes).
+inline bool batch2_keys_fit(long long n, long long Q, long long K)
+{
+    return K * (n * Q + 65535 + Q) + n < (1LL << 31);
+}
 cudaError_t launch_split_batch_i16_cap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,
                                        int *blocks_per_sm, cudaStream_t stream);
 cudaError_t launch_split_batch_i16_nocap(const BatchParams &b, const DequeShape &shape, int grid, bool configure_only,

@@ -156,6 +156,7 @@ int cvrpsd_split_eval_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, 
     bp.list = ctx->mt_list;
     bp.list_cap = ctx->mt_list_cap;
     bp.max_n = n;
+    bp.walk2 = demand_dtype == CVRPSD_I16 && batch2_keys_fit(n, Q, K);
     int per_sm = 0;
     CK(launch_split_batch(bp, demand_dtype, L < n, shape, 0, true, &per_sm, stream), "configure batch kernel");
     CK(launch_split_batch(bp, demand_dtype, L < n, shape, ctx->sm_count * (per_sm > 0 ? per_sm : 1), false, nullptr,

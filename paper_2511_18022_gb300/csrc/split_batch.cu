@@ -119,6 +119,9 @@ cudaError_t launch_split_batch_i16_cap(const BatchParams &b, const DequeShape &s
 cudaError_t launch_split_batch(const BatchParams &b, int esize, bool lcap, const DequeShape &shape, int grid,
                                bool configure_only, int *blocks_per_sm, cudaStream_t stream)
 {
+    if (esize == 2 && b.walk2 && batch2_shape_compiled(shape))
+        return lcap ? launch_split_batch2_cap(b, shape, grid, configure_only, blocks_per_sm, stream)
+                    : launch_split_batch2_nocap(b, shape, grid, configure_only, blocks_per_sm, stream);
     if (esize == 2)
         return lcap ? launch_split_batch_i16_cap(b, shape, grid, configure_only, blocks_per_sm, stream)
                     : launch_split_batch_i16_nocap(b, shape, grid, configure_only, blocks_per_sm, stream);

@@ -149,6 +149,7 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     w.out_cost = p.out_cost;
     w.acc = p.acc;
     w.ovf_list = p.ovf_list;
+    w.status = p.acc + ACC_STATUS;
     w.pitch = (uint32_t)pitch;
     const long long tiles = (p.S + s.threads - 1) / s.threads;
     const long long grid = rounds > 0 ? (tiles + rounds - 1) / rounds : tiles;

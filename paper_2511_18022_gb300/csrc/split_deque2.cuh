@@ -201,19 +201,19 @@ template <typename DT> struct Dem2;
 template <> struct Dem2<int16_t> { using T = unsigned short; };
 template <> struct Dem2<int32_t> { using T = unsigned int; };
 
-template <typename DT, int CAP>
-__device__ __forceinline__ uint32_t load_dem2(const char *base, const TabParam<CAP> &tab, int i, uint32_t pitch,
+template <typename DT, typename TB>
+__device__ __forceinline__ uint32_t load_dem2(const char *base, const TB &tab, int i, uint32_t pitch,
                                               int n, unsigned long long *status)
 {
-    if (!index_ok(i >= 1 && i <= n && i <= CAP, status)) return 0u;
-    const uint32_t row = tab.e[i - 1].x & kTab2RowMask;
+    if (!index_ok(i >= 1 && i <= n && i <= TB::kCap, status)) return 0u;
+    const uint32_t row = tab.row(i);
     if (!index_ok(row < (uint32_t)n, status)) return 0u;
     return (uint32_t)__ldcs(reinterpret_cast<const typename Dem2<DT>::T *>(base + (unsigned long long)row * pitch));
 }
 
 // Positions i0 .. i0 + kPrefetch2 - 1 (GUARD: the block may reach past n).
-template <typename DT, int R, int T, bool LTEST, bool OVF, bool NOWRAP, bool GUARD, bool GENERAL, int CAP>
-__device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
+template <typename DT, int R, int T, bool LTEST, bool OVF, bool NOWRAP, bool GUARD, bool GENERAL, typename TB>
+__device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TB &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs, int &out)
 {
     constexpr bool CLAMP = sizeof(DT) == 4;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void walk2_steps(Deque2 &d, const uint32_t (&q)[kPref
     for (int u = 0; u < kPrefetch2; ++u) {
         const int i = i0 + u;
         if (GUARD && i > n) break;
-        const uint2 e = tab.e[i - 1];
+        const uint2 e = tab.entry(i);
         const int ci = (int)e.y;
         const bool noback = (e.x & kTab2NoBack) != 0;
         const uint32_t xi = QK + (uint32_t)i;
@@ -248,14 +248,13 @@ __device__ __forceinline__ bool walk2_exact(const Deque2 &d, int i0, uint32_t K,
     return __any_sync(0xffffffffu, risk);
 }
 
-template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, int CAP>
-__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TabParam<CAP> &tab,
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, bool GUARD, typename TB>
+__device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPrefetch2], const TB &tab,
                                             int i0, int n, uint32_t K, uint32_t QK, int L, int Q, uint32_t rs,
                                             bool exact, int &out)
 {
     constexpr bool kBlockOvf = block_ovf<R>();
-    const int m = (i0 - 1) / kPrefetch2;
-    const bool general = (tab.nonpos[m >> 5] >> (m & 31)) & 1u;
+    const bool general = tab.general(i0);
     if (exact) {
         if (general)
             walk2_steps<DT, R, T, LCAP, true, NOWRAP, GUARD, true>(d, q, tab, i0, n, K, QK, L, Q, rs, out);
@@ -269,8 +268,8 @@ __device__ __forceinline__ void walk2_block(Deque2 &d, const uint32_t (&q)[kPref
     }
 }
 
-template <typename DT, bool CLAMPI, int CAP>
-__device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> &tab, int i0, int n, uint32_t pitch,
+template <typename DT, bool CLAMPI, typename TB>
+__device__ __forceinline__ void prefetch2(const char *base, const TB &tab, int i0, int n, uint32_t pitch,
                                           unsigned long long *status, uint32_t (&q)[kPrefetch2])
 {
 #pragma unroll
@@ -281,8 +280,8 @@ __device__ __forceinline__ void prefetch2(const char *base, const TabParam<CAP> 
 // The walk of one scenario (column s; a thread past S walks column 0 and
 // reports nothing: every lane takes part in the votes). Returns f(n) or
 // sets *aside.
-template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
-__device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabParam<CAP> &tab, long long s,
+template <typename DT, int R, int T, bool LCAP, bool NOWRAP, typename TB>
+__device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TB &tab, long long s,
                                               uint32_t rs, uint32_t slot0, bool &aside)
 {
     const int n = p.n, Q = p.Q, L = p.L;
@@ -300,7 +299,7 @@ __device__ __forceinline__ int walk2_scenario(const Walk2Params &p, const TabPar
     int out = 0;
     uint32_t qa[kPrefetch2], qb[kPrefetch2];
     const uint32_t pitch = p.pitch;
-    unsigned long long *status = p.acc + ACC_STATUS;
+    unsigned long long *status = p.status;
     prefetch2<DT, true>(base, tab, 1, n, pitch, status, qa);
     int i0 = 1;
     // One exactness vote covers both prefetch blocks of an iteration.
@@ -355,7 +354,7 @@ __global__ void __launch_bounds__(T, d2_min_blocks<R, T>()) split_deque2_kernel(
         if (s < p.S) {
             if (aside) {
                 const unsigned long long idx = atomicAdd(p.acc + ACC_OVERFLOW, 1ull);
-                if (index_ok(idx < (unsigned long long)p.S, p.acc + ACC_STATUS)) p.ovf_list[idx] = (int32_t)s;
+                if (index_ok(idx < (unsigned long long)p.S, p.status)) p.ovf_list[idx] = (int32_t)s;
             } else {
                 sum += c;
                 if (p.out_cost) p.out_cost[s] = c;
