@@ -1,9 +1,10 @@
 // Surrogate network for screening local-search neighbours: training and
 // inference kernels. BF16 weights, per-position features as BF16 hi + lo
-// pairs (about 16 significant bits), FP32 activations and accumulation. Layer 1's forward pass runs on the tensor
+// pairs (about 16 significant bits), FP32 activations and accumulation.
+// The products of layers 1 and 2, forward and backward, run on the tensor
 // cores (mlp_tc.cu); this file holds the rest: the backward pass of layer 1
-// (which recomputes the pre-activations from the same BF16 operands), the
-// layer 2 products, the output layer, the loss and Adam.
+// (which recomputes the pre-activations from the same operands), the output
+// layer, the loss, the bias gradients and Adam.
 //
 // Architecture (width H = 256):
 //   per position k of a tour:  phi_k = (x, y, mu / Q, sd / Q, frac(cum_k / Q))
@@ -126,80 +127,6 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
     }
 }
 
-// ---------------------------------------------------------------- GEMMs
-// Backward-pass products on the CUDA cores: 32 x 32 output tile per block of
-// 256 threads (4 outputs per thread), the reduction dimension in chunks of 32
-// through shared memory.
-
-// out[b][k] = sum_o G[b][o] W[o][k]                     G fp32, W bf16 [N][ldw]
-__global__ void __launch_bounds__(256) gemm_gw_kernel(const float *G, int B, int N, int ldg, const __nv_bfloat16 *W,
-                                                      int Kd, int ldw, float *out, int ldo)
-{
-    __shared__ float sg[32][33], sw[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int b0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    float acc[4] = {0, 0, 0, 0};
-    for (int o0 = 0; o0 < N; o0 += 32) {
-        for (int r = ty; r < 32; r += 8) {
-            const int b = b0 + r, o = o0 + tx;
-            sg[r][tx] = (b < B && o < N) ? G[(long long)b * ldg + o] : 0.0f;
-            const int oo = o0 + r, kk = k0 + tx;
-            sw[r][tx] = (oo < N && kk < Kd) ? __bfloat162float(W[(long long)oo * ldw + kk]) : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int o = 0; o < 32; ++o) {
-            const float wv = sw[o][tx];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += sg[ty + 8 * q][o] * wv;
-        }
-        __syncthreads();
-    }
-    const int k = k0 + tx;
-    if (k >= Kd) return;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int b = b0 + ty + 8 * q;
-        if (b < B) out[(long long)b * ldo + k] = acc[q];
-    }
-}
-
-// out[o][k] += sum_b G[b][o] X[b][k]                    G, X fp32 (weight gradient)
-// The batch splits into slabs of kGtxSlab rows (blockIdx.z), each adding its
-// partial sums with atomics, so that a large batch fills the GPU.
-constexpr int kGtxSlab = 512;
-__global__ void __launch_bounds__(256) gemm_gtx_kernel(const float *G, int B, int N, int ldg, const float *X, int Kd,
-                                                       int ldx, float *out, int ldo)
-{
-    __shared__ float sg[32][33], sx[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    const int bz0 = blockIdx.z * kGtxSlab, bz1 = min(B, bz0 + kGtxSlab);
-    float acc[4] = {0, 0, 0, 0};
-    for (int b0 = bz0; b0 < bz1; b0 += 32) {
-        for (int r = ty; r < 32; r += 8) {
-            const int b = b0 + r;
-            sg[r][tx] = (b < bz1 && o0 + tx < N) ? G[(long long)b * ldg + o0 + tx] : 0.0f;
-            sx[r][tx] = (b < bz1 && k0 + tx < Kd) ? X[(long long)b * ldx + k0 + tx] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
-            const float xv = sx[b][tx];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += sg[b][ty + 8 * q] * xv;
-        }
-        __syncthreads();
-    }
-    const int k = k0 + tx;
-    if (k >= Kd) return;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int o = o0 + ty + 8 * q;
-        if (o < N) atomicAdd(out + (long long)o * ldo + k, acc[q]);
-    }
-}
-
 // ---------------------------------------------------------------- layer 3, loss
 
 // y[b] = w3 . u_b + b3; with targets: dy = 2 (y - target) / B, loss partials.
@@ -277,7 +204,6 @@ __global__ void to_bf16_kernel(const float *p, __nv_bfloat16 *q, long long P)
 
 // ---------------------------------------------------------------- host launchers
 
-static dim3 grid2(int cols, int rows) { return dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)); }
 
 cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U, float *y, const float *target,
                         float *dy, float *loss, cudaStream_t st)
@@ -298,17 +224,17 @@ cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const fl
     float *gw1 = grad + kOffW1, *gb1 = grad + kOffB1, *gw2 = grad + kOffW2, *gb2 = grad + kOffB2;
     float *gw3 = grad + kOffW3, *gb3 = grad + kOffB3;
     mlp_out_backward_kernel<<<T < 512 ? T : 512, kMlpH, 0, st>>>(U, T, dy, wt.w3, dU, gw3, gb3);
-    dim3 g3 = grid2(kMlpIn2, kMlpH);
-    g3.z = (unsigned)((T + kGtxSlab - 1) / kGtxSlab);
-    gemm_gtx_kernel<<<g3, 256, 0, st>>>(dU, T, kMlpH, kMlpH, l1.zt, kMlpIn2, kMlpIn2, gw2, kMlpIn2);
+    cudaError_t e = mlp_grad_w2_tc(dU, l1.zt, T, gw2, l1.err, st);
+    if (e != cudaSuccess) return e;
     colsum_kernel<<<dim3(1, (unsigned)((T + 63) / 64)), kMlpH, 0, st>>>(dU, T, kMlpH, kMlpH, gb2);
-    gemm_gw_kernel<<<grid2(kMlpIn2, T), 256, 0, st>>>(dU, T, kMlpH, kMlpH, wt.w2, kMlpIn2, kMlpIn2, dzt, kMlpIn2);
+    e = mlp_grad_zt_tc(dU, T, wt.w2, dzt, l1.err, st);
+    if (e != cudaSuccess) return e;
     MlpLayer1Args b = l1;
     b.dzt = dzt;
     b.gw1 = gw1;
     b.gb1 = gb1;
     const size_t smem = (size_t)l1.n * 5 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(mlp_layer1_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(mlp_layer1_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     mlp_layer1_kernel<true><<<T < 16384 ? T : 16384, kMlpH, smem, st>>>(b);

@@ -46,6 +46,12 @@ cudaError_t mlp_layer1_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st
 cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const __nv_bfloat16 *b2, float *U,
                           unsigned int *err, cudaStream_t st);
 
+// Backward products on the tensor cores (mlp_tc.cu): dZT = dU W2 and
+// gW2 += dU^T ZT (FP32 operands as BF16 hi/lo pairs, FP32 accumulation).
+cudaError_t mlp_grad_zt_tc(const float *dU, int T, const __nv_bfloat16 *w2, float *dzt, unsigned int *err,
+                           cudaStream_t st);
+cudaError_t mlp_grad_w2_tc(const float *dU, const float *zt, int T, float *gw2, unsigned int *err, cudaStream_t st);
+
 cudaError_t mlp_forward(const MlpLayer1Args &l1, const MlpWeights &wt, float *U, float *y, const float *target,
                         float *dy, float *loss, cudaStream_t st);
 cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const float *U, const float *dy, float *dU,

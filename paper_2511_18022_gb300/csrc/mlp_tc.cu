@@ -320,6 +320,179 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const floa
     if (w == 0) tc::tmem_dealloc(tmem, kL2TmemCols);
 }
 
+// ---------------------------------------------------------------- backward GEMMs
+//
+// C (M x N) = A (M x K) B (N x K)^T on the tensor cores, stored or added
+// atomically (split-K over blockIdx.z). One CTA computes a 128 x 160 tile of C
+// in tensor memory, K in chunks of 64 staged in shared memory in the K-major
+// layout of the forward kernels. FP32 operands are split into BF16 hi and
+// lo parts (hi = bf16(v), lo = bf16(v - hi)); a product of two split
+// operands takes hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
+// rounding of the sum), one with an exact BF16 operand hi*B + lo*B. Operands
+// are read through an element rule: A(m, k) at a[m * lda + k], or at
+// a[k * lda + m] when transposed (AT); B likewise (BT), FP32 or BF16.
+constexpr int kGM = 128;                       // rows of C per CTA
+constexpr int kGN = 160;                       // columns of C per CTA (5 x 32)
+constexpr int kGK = 64;                        // K per staged chunk
+constexpr int kGKc = kGK / 8;                  // 16-byte core-matrix columns per row group
+constexpr size_t kGA = (size_t)kGM * kGK * 2;  // one BF16 A part
+constexpr size_t kGB = (size_t)kGN * kGK * 2;  // one BF16 B part
+constexpr size_t kGSmem = 2 * kGA + 2 * kGB;   // A hi, A lo, B hi, B lo
+// Requested dynamic shared memory: the operands plus padding so that at
+// most two CTAs share an SM (each holds 256 TMEM columns).
+constexpr size_t kGSmemReq = 100 * 1024;
+constexpr uint32_t kGTmemCols = 256;
+
+struct TcGemm {
+    const float *a;          // FP32 A
+    int lda;
+    const float *bf;         // FP32 B (or nullptr)
+    const __nv_bfloat16 *bh; // BF16 B (or nullptr)
+    int ldb;
+    int M, N, K;
+    int k_slab;              // K per blockIdx.z
+    float *out;
+    int ldo;
+    unsigned int *err;
+};
+
+template <bool AT, bool BT, bool BBF16, bool ATOMIC>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(TcGemm g)
+{
+    extern __shared__ __align__(128) unsigned char smem[];   // A hi | A lo | B hi | B lo
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    unsigned char *a_hi = smem, *a_lo = smem + kGA, *b_hi = smem + 2 * kGA, *b_lo = smem + 2 * kGA + kGB;
+    const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+    const int k_begin = blockIdx.z * g.k_slab, k_end = min(g.K, k_begin + g.k_slab);
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    if (j == 0) tc::mbar_init(mbar);
+    if (w == 0) tc::tmem_alloc((uint32_t)__cvta_generic_to_shared(&s_tmem), kGTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    uint32_t parity = 0;
+    bool ok = true, any = false;
+    for (int kc0 = k_begin; kc0 < k_end; kc0 += kGK) {
+        // A: item = (row, group of 8 K columns); transposed operands read the
+        // row index fastest, so neighbouring threads read neighbouring words
+        for (int e = j; e < kGM * kGKc; e += kTcThreads) {
+            const int r = AT ? e % kGM : e / kGKc, gk = AT ? e / kGM : e % kGKc;
+            const int m = m0 + r;
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __nv_bfloat16 hi[2], lo[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kc0 + 8 * gk + 2 * q + h;
+                    float v = 0.0f;
+                    if (m < g.M && k < k_end) v = AT ? g.a[(long long)k * g.lda + m] : g.a[(long long)m * g.lda + k];
+                    hi[h] = __float2bfloat16_rn(v);
+                    lo[h] = __float2bfloat16_rn(v - __bfloat162float(hi[h]));
+                }
+                ph[q] = pack_bf16x2(hi[0], hi[1]);
+                pl[q] = pack_bf16x2(lo[0], lo[1]);
+            }
+            const uint32_t off = tc::kmajor_offset(r, 8 * gk, kGKc);
+            *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+        for (int e = j; e < kGN * kGKc; e += kTcThreads) {
+            const int r = BT ? e % kGN : e / kGKc, gk = BT ? e / kGN : e % kGKc;
+            const int nn = n0 + r;
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __nv_bfloat16 hi[2], lo[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kc0 + 8 * gk + 2 * q + h;
+                    const bool in = nn < g.N && k < k_end;
+                    if (BBF16) {
+                        hi[h] = in ? (BT ? g.bh[(long long)k * g.ldb + nn] : g.bh[(long long)nn * g.ldb + k])
+                                   : __float2bfloat16_rn(0.0f);
+                        lo[h] = __float2bfloat16_rn(0.0f);
+                    } else {
+                        const float v = in ? (BT ? g.bf[(long long)k * g.ldb + nn] : g.bf[(long long)nn * g.ldb + k])
+                                           : 0.0f;
+                        hi[h] = __float2bfloat16_rn(v);
+                        lo[h] = __float2bfloat16_rn(v - __bfloat162float(hi[h]));
+                    }
+                }
+                ph[q] = pack_bf16x2(hi[0], hi[1]);
+                pl[q] = pack_bf16x2(lo[0], lo[1]);
+            }
+            const uint32_t off = tc::kmajor_offset(r, 8 * gk, kGKc);
+            *reinterpret_cast<uint4 *>(b_hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            if (!BBF16) *reinterpret_cast<uint4 *>(b_lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+        tc::fence_operands();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (j == 0) {
+            const uint32_t idesc = tc::instr_desc(kGN);
+            const uint32_t sah = (uint32_t)__cvta_generic_to_shared(a_hi), sal = (uint32_t)__cvta_generic_to_shared(a_lo);
+            const uint32_t sbh = (uint32_t)__cvta_generic_to_shared(b_hi), sbl = (uint32_t)__cvta_generic_to_shared(b_lo);
+            const uint32_t sbo = kGKc * 128;
+            for (int step = 0; step < kGK / 16; ++step) {
+                const uint32_t koff = (uint32_t)step * 256;
+                const uint64_t ah = tc::smem_desc(sah + koff, 128, sbo), al = tc::smem_desc(sal + koff, 128, sbo);
+                const uint64_t bh = tc::smem_desc(sbh + koff, 128, sbo);
+                tc::mma_bf16(tmem, ah, bh, idesc, any || step > 0);
+                tc::mma_bf16(tmem, al, bh, idesc, true);
+                if (!BBF16) tc::mma_bf16(tmem, ah, tc::smem_desc(sbl + koff, 128, sbo), idesc, true);
+            }
+            tc::mma_commit(mbar);
+        }
+        any = true;
+        // the operands are overwritten next chunk: wait for the MMAs
+        ok = tc::mbar_wait(mbar, parity);
+        parity ^= 1u;
+        if (!ok && lane == 0) atomicOr(g.err, 1u);
+        tc::fence_after_sync();
+        __syncthreads();
+        if (!ok) break;
+    }
+    if (ok && any && w < 4) {
+        const int m = m0 + 32 * w + lane;
+        const uint32_t row = tmem + ((uint32_t)(32 * w) << 16);
+#pragma unroll 1
+        for (int c = 0; c < kGN; c += 32) {
+            float r[32];
+            tc::tmem_ld32(row + c, r);
+            if (m < g.M) {
+                float *out = g.out + (long long)m * g.ldo + n0 + c;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    if (n0 + c + q < g.N) {
+                        if (ATOMIC) atomicAdd(out + q, r[q]);
+                        else out[q] = r[q];
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tmem, kGTmemCols);
+}
+
+template <bool AT, bool BT, bool BBF16, bool ATOMIC>
+cudaError_t tc_gemm(const TcGemm &g, cudaStream_t st)
+{
+    auto kern = tc_gemm_kernel<AT, BT, BBF16, ATOMIC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmemReq);
+    if (e != cudaSuccess) return e;
+    const int slabs = (g.K + g.k_slab - 1) / g.k_slab;
+    const dim3 grid((unsigned)((g.M + kGM - 1) / kGM), (unsigned)((g.N + kGN - 1) / kGN), (unsigned)slabs);
+    kern<<<grid, kTcThreads, kGSmemReq, st>>>(g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const __nv_bfloat16 *b2, float *U,
@@ -341,6 +514,45 @@ cudaError_t mlp_layer1_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st
     const int grid = l1.T < sm_count ? l1.T : sm_count;
     mlp_layer1_tc_kernel<<<grid, kTcThreads, kTcSmemPad, st>>>(l1);
     return cudaGetLastError();
+}
+
+// dZT (T x 257) = dU (T x 256) W2 (256 x 257): A = dU, B(n, k) = W2[k][n].
+cudaError_t mlp_grad_zt_tc(const float *dU, int T, const __nv_bfloat16 *w2, float *dzt, unsigned int *err,
+                           cudaStream_t st)
+{
+    TcGemm g{};
+    g.a = dU;
+    g.lda = kMlpH;
+    g.bh = w2;
+    g.ldb = kMlpIn2;
+    g.M = T;
+    g.N = kMlpIn2;
+    g.K = kMlpH;
+    g.k_slab = kMlpH;
+    g.out = dzt;
+    g.ldo = kMlpIn2;
+    g.err = err;
+    return tc_gemm<false, true, true, false>(g, st);
+}
+
+// gW2 (256 x 257) += dU^T (256 x T) ZT (T x 257): A(m, k) = dU[k][m],
+// B(n, k) = ZT[k][n]; split-K over slabs of 128 tours (a CTA per slab and
+// tile fills the GPU), added atomically.
+cudaError_t mlp_grad_w2_tc(const float *dU, const float *zt, int T, float *gw2, unsigned int *err, cudaStream_t st)
+{
+    TcGemm g{};
+    g.a = dU;
+    g.lda = kMlpH;
+    g.bf = zt;
+    g.ldb = kMlpIn2;
+    g.M = kMlpH;
+    g.N = kMlpIn2;
+    g.K = T;
+    g.k_slab = 128;
+    g.out = gw2;
+    g.ldo = kMlpIn2;
+    g.err = err;
+    return tc_gemm<true, true, false, true>(g, st);
 }
 
 }  // namespace cvrpsd

@@ -197,3 +197,37 @@ def test_batch_autotune_dtype_arm_skips_int16_when_demands_do_not_fit(sp, cv):
     tours = [dict(tour=i.tour, dist=i.dist, demand=dev(m), Q=i.Q, L=i.L) for i, m in zip(insts, mats32)]
     r = sp.batch_autotune(tours, S)
     assert r["dtype"] == cv.I32 and r["shapes_timed"] == 20
+
+
+@pytest.mark.parametrize("shape", [(64, 1, 16), (128, 1, 32), (256, 1, 16)])
+def test_batch_second_walk_general_blocks_and_overflow(sp, cv, shape):
+    """int16 demands with one scenario per thread run the batch on the second
+    walk. Customers on a line through the depot, visited on alternating
+    sides, make C_i = 0 at most positions (blocks of the emptying back walk);
+    all-zero demand columns make the deque hold the whole window (ring
+    overflow, set aside) unless the route-length cap L bounds it; a demand
+    above Q makes a scenario infeasible. Every cost against the oracle."""
+    n, S = 70, 2049
+    coords = [[0, 0]] + [[(7 * ((k + 1) // 2)) * (1 if k % 2 else -1), 0] for k in range(1, n + 1)]
+    line = instance_from_coords(coords, list(range(1, n + 1)), Q=50)
+    sig = [0] + list(line.tour)
+    C = [line.dist[sig[i], 0] + line.dist[0, sig[i + 1]] - line.dist[sig[i], sig[i + 1]] for i in range(1, n)]
+    assert sum(c <= 0 for c in C) > n // 2
+    rng = np.random.default_rng(8)
+    D1 = rng.integers(0, 13, size=(n, S)).astype(np.int16)
+    D1[:, :40] = 0                                  # whole-tour windows
+    D1[9, 777] = 51                                 # above Q
+    other = make_instance(150, 1, 10, seed=21, Q=45)
+    D2 = demand_matrix(other.mu, other.region, 1, 4, S, dtype=np.int16)
+    D2[:, 1000:1010] = 0
+    cases = [(line, D1, n), (line, D1, 6), (other, D2, 9)]
+    outs = [torch.empty(S, dtype=torch.int32, device="cuda") for _ in cases]
+    tours = [dict(tour=i.tour, dist=i.dist, demand=dev(D), Q=i.Q, L=L, out_cost=o)
+             for (i, D, L), o in zip(cases, outs)]
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=shape[0], spt=shape[1], ring=shape[2])
+    res = sp.split_batch(tours, S)
+    for t, ((inst, D, L), o) in enumerate(zip(cases, outs)):
+        want, wsum, winf, _ = oracle.split_costs(inst.tour, inst.dist, D, inst.Q, L, nthreads=8)
+        assert np.array_equal(o.cpu().numpy(), want), f"tour {t}"
+        assert (res["sum"][t], res["infeasible"][t]) == (wsum, winf), f"tour {t}"
+    assert res["infeasible"][0] >= 1 and sp.stats()["overflow"] > 0
