@@ -26,23 +26,27 @@
 
 namespace cvrpsd {
 
-// ---------------------------------------------------------------- layer 1
+// ---------------------------------------------------------------- layer 1 backward
 
-// One block (H threads) per tour: features in shared memory, then thread j
-// accumulates relu(pre_kj) over the positions. TRAIN=false writes z and t;
-// BACKWARD=true instead reads dz and accumulates dW1 / db1.
-template <bool BACKWARD>
-__global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
+// dW1 and db1. Blocks of H threads loop over tours; per tour the features go
+// to shared memory (the same BF16 pairs as the tensor-core forward pass) and
+// thread j recomputes its pre-activation at each position and, where it is
+// positive, adds the features (and 1 for the bias), scaled by dz_j / n. Each
+// thread keeps its six sums across the block's tours and adds them to the
+// gradient once.
+__global__ void __launch_bounds__(kMlpH) mlp_layer1_backward_kernel(MlpLayer1Args a)
 {
     extern __shared__ float feat[];           // [n][5]
     __shared__ float s_part[kMlpH / 32];
     __shared__ float s_carry;
     const int n = a.n, j = threadIdx.x, lane = j & 31, w = j >> 5;
-    const long long N1 = (long long)n + 1;
+    float wj[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) wj[f] = __bfloat162float(a.w1[j * 5 + f]);
+    const float bj = __bfloat162float(a.b1[j]);
+    float gw[5] = {0, 0, 0, 0, 0}, gb = 0.0f;
     for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
         const int32_t *tour = a.tours + (long long)t * n;
-        // features and the tour length
-        float len = 0.0f;
         if (j == 0) s_carry = 0.0f;
         __syncthreads();
         for (int k0 = 0; k0 < n; k0 += kMlpH) {
@@ -52,9 +56,6 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
             if (k < n) {
                 c = min(max(tour[k], 1), n);
                 m = a.cust[(c - 1) * 4 + 2];
-                const int nx = k + 1 < n ? min(max(tour[k + 1], 1), n) : 0;
-                len += (float)a.dist[(long long)c * N1 + nx];
-                if (k == 0) len += (float)a.dist[c];
             }
             // inclusive scan of mu / Q over this chunk
             float v = m;
@@ -71,60 +72,40 @@ __global__ void __launch_bounds__(kMlpH) mlp_layer1_kernel(MlpLayer1Args a)
             if (k < n) {
                 // features as the tensor-core forward pass takes them: the sum
                 // of a BF16 pair hi = bf16(v), lo = bf16(v - hi)
-                const float v[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
-                                          a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
+                const float v5[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
+                                           a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
                 float *f = feat + 5 * k;
 #pragma unroll
                 for (int q = 0; q < kMlpIn1; ++q) {
-                    const float hi = __bfloat162float(__float2bfloat16_rn(v[q]));
-                    f[q] = hi + __bfloat162float(__float2bfloat16_rn(v[q] - hi));
+                    const float hi = __bfloat162float(__float2bfloat16_rn(v5[q]));
+                    f[q] = hi + __bfloat162float(__float2bfloat16_rn(v5[q] - hi));
                 }
             }
             __syncthreads();
             if (j == kMlpH - 1) s_carry = cum;
             __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
-        if (lane == 0) s_part[w] = len;
-        __syncthreads();
-        float tl = 0.0f;
-        for (int q = 0; q < kMlpH / 32; ++q) tl += s_part[q];
-        tl = (tl - a.len_mean) * a.len_inv_sd;
-
-        float wj[5];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) wj[f] = __bfloat162float(a.w1[j * 5 + f]);
-        const float bj = __bfloat162float(a.b1[j]);
-        if (!BACKWARD) {
-            float acc = 0.0f;
+        const float g = a.dzt[(long long)t * kMlpIn2 + j] / (float)n;
+        if (g != 0.0f) {
+            float sw[5] = {0, 0, 0, 0, 0}, sb = 0.0f;
             for (int k = 0; k < n; ++k) {
                 const float *f = feat + 5 * k;
                 const float pre = bj + wj[0] * f[0] + wj[1] * f[1] + wj[2] * f[2] + wj[3] * f[3] + wj[4] * f[4];
-                acc += fmaxf(pre, 0.0f);
-            }
-            a.zt[(long long)t * kMlpIn2 + j] = acc / (float)n;
-            if (j == 0) a.zt[(long long)t * kMlpIn2 + kMlpH] = tl;
-        } else {
-            const float g = a.dzt[(long long)t * kMlpIn2 + j] / (float)n;
-            float gw[5] = {0, 0, 0, 0, 0}, gb = 0.0f;
-            if (g != 0.0f) {
-                for (int k = 0; k < n; ++k) {
-                    const float *f = feat + 5 * k;
-                    const float pre = bj + wj[0] * f[0] + wj[1] * f[1] + wj[2] * f[2] + wj[3] * f[3] + wj[4] * f[4];
-                    if (pre > 0.0f) {
+                if (pre > 0.0f) {
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) gw[q] += f[q];
-                        gb += 1.0f;
-                    }
+                    for (int q = 0; q < 5; ++q) sw[q] += f[q];
+                    sb += 1.0f;
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 5; ++q) atomicAdd(a.gw1 + j * 5 + q, g * gw[q]);
-            atomicAdd(a.gb1 + j, g * gb);
+            for (int q = 0; q < 5; ++q) gw[q] += g * sw[q];
+            gb += g * sb;
         }
-        __syncthreads();
+        __syncthreads();                          // feat is rewritten for the next tour
     }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) atomicAdd(a.gw1 + j * 5 + q, gw[q]);
+    atomicAdd(a.gb1 + j, gb);
 }
 
 // ---------------------------------------------------------------- layer 3, loss
@@ -234,10 +215,11 @@ cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const fl
     b.gw1 = gw1;
     b.gb1 = gb1;
     const size_t smem = (size_t)l1.n * 5 * sizeof(float);
-    e = cudaFuncSetAttribute(mlp_layer1_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(mlp_layer1_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    mlp_layer1_kernel<true><<<T < 16384 ? T : 16384, kMlpH, smem, st>>>(b);
+    // a few blocks per SM, each over many tours: one gradient update per block
+    const int blocks = 4 * (l1.sm_count > 0 ? l1.sm_count : 152);
+    mlp_layer1_backward_kernel<<<T < blocks ? T : blocks, kMlpH, smem, st>>>(b);
     return cudaGetLastError();
 }
 
