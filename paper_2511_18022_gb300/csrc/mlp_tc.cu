@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_layer2_tc_kernel(const floa
 // in tensor memory, K in chunks of 64 staged in shared memory in the K-major
 // layout of the forward kernels. FP32 operands are split into BF16 hi and
 // lo parts (hi = bf16(v), lo = bf16(v - hi)); a product of two split
-// operands takes hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
-// rounding of the sum), one with an exact BF16 operand hi*B + lo*B. Operands
+// operands takes hi*hi + hi*lo + lo*hi (the lo*lo term, at most 2^-18 of
+// the product, is the order of the pair's own rounding and is left out),
+// one with an exact BF16 operand hi*B + lo*B. Operands
 // are read through an element rule: A(m, k) at a[m * lda + k], or at
 // a[k * lda + m] when transposed (AT); B likewise (BT), FP32 or BF16.
 constexpr int kGM = 128;                       // rows of C per CTA
