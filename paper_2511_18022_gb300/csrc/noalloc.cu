@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "../../include/cvrpsd.h"
+#include "deque2.h"
 #include "kernels.h"
 #include "trace.h"
 #include "tour_table.h"
@@ -146,9 +147,17 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
     TourStep *tab = reinterpret_cast<TourStep *>(ds.scratch + kAccBytes);
     int32_t *list = reinterpret_cast<int32_t *>(ds.scratch + kAccBytes + kTabBytes);
 
-    int32_t g0 = 0;
+    // The accumulators keep the previous call's values: start this call at zero.
+    if (cudaMemsetAsync(acc, 0, ACC_WORDS * sizeof(unsigned long long), stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CVRPSD_ERR_CUDA;
+    }
+    // The shared host table is read by the upload and, for the parameter-table
+    // walk, by the launch (its parameters are copied when it is enqueued):
+    // both happen under the lock.
     {
         std::lock_guard<std::mutex> lock(g_host_mutex);
+        int32_t g0 = 0;
         char msg[256];
         const int rc = fill_tour_table(tour, n, dist, Q, g_host_tab, &g0, msg, sizeof(msg));
         if (rc) return rc;
@@ -158,37 +167,42 @@ extern "C" int cvrpsd_split_eval_noalloc(const int32_t *tour, int32_t n, const i
             cudaGetLastError();
             return CVRPSD_ERR_CUDA;
         }
-    }
-    // The accumulators keep the previous call's values: start this call at zero.
-    if (cudaMemsetAsync(acc, 0, ACC_WORDS * sizeof(unsigned long long), stream) != cudaSuccess) {
-        cudaGetLastError();
-        return CVRPSD_ERR_CUDA;
-    }
 
-    if (S > 0) {
-        SplitParams p{};
-        p.tab = tab;
-        p.demand = demand;
-        p.ld = ld;
-        p.S = S;
-        p.n = n;
-        p.Q = Q;
-        p.L = L;
-        p.g0 = g0;
-        p.K = key_scale(n);
-        p.out_cost = out_cost;
-        p.acc = acc;
-        p.ovf_list = list;
-        DequeShape shape{128, 1, 16};
-        while (split_deque_smem(p, shape) > (size_t)ds.max_smem) {
-            if (shape.threads > 64) shape.threads >>= 1;
-            else return CVRPSD_ERR_UNSUPPORTED;
-        }
-        if (launch_split_deque(p, demand_dtype, shape, stream) != cudaSuccess ||
-            launch_split_warp(p, demand_dtype, list, acc + ACC_OVERFLOW, 2 * ds.sm_count, ds.max_smem, stream) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            return CVRPSD_ERR_CUDA;
+
+        if (S > 0) {
+            SplitParams p{};
+            p.tab = tab;
+            p.demand = demand;
+            p.ld = ld;
+            p.S = S;
+            p.n = n;
+            p.Q = Q;
+            p.L = L;
+            p.g0 = g0;
+            p.K = key_scale(n);
+            p.out_cost = out_cost;
+            p.acc = acc;
+            p.ovf_list = list;
+            // The parameter-table walk where it applies (no device memory beyond
+            // the fixed scratch: its table travels in the launch parameters),
+            // else the global-table walk.
+            DequeShape shape{128, 1, 16};
+            cudaError_t e = cudaSuccess;
+            if (deque2_supported(p, demand_dtype)) {
+                e = launch_split_deque2(p, g_host_tab, demand_dtype, shape, 0, nullptr, stream);
+            } else {
+                while (split_deque_smem(p, shape) > (size_t)ds.max_smem) {
+                    if (shape.threads > 64) shape.threads >>= 1;
+                    else return CVRPSD_ERR_UNSUPPORTED;
+                }
+                e = launch_split_deque(p, demand_dtype, shape, stream);
+            }
+            if (e != cudaSuccess ||
+                launch_split_warp(p, demand_dtype, list, acc + ACC_OVERFLOW, 2 * ds.sm_count, ds.max_smem, stream) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                return CVRPSD_ERR_CUDA;
+            }
         }
     }
     if (!out_sum && !out_infeasible && !out_mean) return CVRPSD_OK;
