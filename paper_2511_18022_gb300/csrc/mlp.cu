@@ -2,9 +2,8 @@
 // inference kernels. BF16 weights, per-position features as BF16 hi + lo
 // pairs (about 16 significant bits), FP32 activations and accumulation.
 // The products of layers 1 and 2, forward and backward, run on the tensor
-// cores (mlp_tc.cu); this file holds the rest: the backward pass of layer 1
-// (which recomputes the pre-activations from the same operands), the output
-// layer, the loss, the bias gradients and Adam.
+// cores (mlp_tc.cu); this file holds the rest: the output layer, the loss,
+// the layer-2 bias gradient and Adam.
 //
 // Architecture (width H = 256):
 //   per position k of a tour:  phi_k = (x, y, mu / Q, sd / Q, frac(cum_k / Q))
@@ -25,88 +24,6 @@
 #include "mlp.h"
 
 namespace cvrpsd {
-
-// ---------------------------------------------------------------- layer 1 backward
-
-// dW1 and db1. Blocks of H threads loop over tours; per tour the features go
-// to shared memory (the same BF16 pairs as the tensor-core forward pass) and
-// thread j recomputes its pre-activation at each position and, where it is
-// positive, adds the features (and 1 for the bias), scaled by dz_j / n. Each
-// thread keeps its six sums across the block's tours and adds them to the
-// gradient once.
-__global__ void __launch_bounds__(kMlpH) mlp_layer1_backward_kernel(MlpLayer1Args a)
-{
-    extern __shared__ float feat[];           // [n][5]
-    __shared__ float s_part[kMlpH / 32];
-    __shared__ float s_carry;
-    const int n = a.n, j = threadIdx.x, lane = j & 31, w = j >> 5;
-    float wj[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) wj[f] = __bfloat162float(a.w1[j * 5 + f]);
-    const float bj = __bfloat162float(a.b1[j]);
-    float gw[5] = {0, 0, 0, 0, 0}, gb = 0.0f;
-    for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
-        const int32_t *tour = a.tours + (long long)t * n;
-        if (j == 0) s_carry = 0.0f;
-        __syncthreads();
-        for (int k0 = 0; k0 < n; k0 += kMlpH) {
-            const int k = k0 + j;
-            float m = 0.0f;
-            int c = 1;
-            if (k < n) {
-                c = min(max(tour[k], 1), n);
-                m = a.cust[(c - 1) * 4 + 2];
-            }
-            // inclusive scan of mu / Q over this chunk
-            float v = m;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            if (lane == 31) s_part[w] = v;
-            __syncthreads();
-            float off = s_carry;
-            for (int q = 0; q < w; ++q) off += s_part[q];
-            const float cum = off + v;
-            if (k < n) {
-                // features as the tensor-core forward pass takes them: the sum
-                // of a BF16 pair hi = bf16(v), lo = bf16(v - hi)
-                const float v5[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
-                                           a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
-                float *f = feat + 5 * k;
-#pragma unroll
-                for (int q = 0; q < kMlpIn1; ++q) {
-                    const float hi = __bfloat162float(__float2bfloat16_rn(v5[q]));
-                    f[q] = hi + __bfloat162float(__float2bfloat16_rn(v5[q] - hi));
-                }
-            }
-            __syncthreads();
-            if (j == kMlpH - 1) s_carry = cum;
-            __syncthreads();
-        }
-        const float g = a.dzt[(long long)t * kMlpIn2 + j] / (float)n;
-        if (g != 0.0f) {
-            float sw[5] = {0, 0, 0, 0, 0}, sb = 0.0f;
-            for (int k = 0; k < n; ++k) {
-                const float *f = feat + 5 * k;
-                const float pre = bj + wj[0] * f[0] + wj[1] * f[1] + wj[2] * f[2] + wj[3] * f[3] + wj[4] * f[4];
-                if (pre > 0.0f) {
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) sw[q] += f[q];
-                    sb += 1.0f;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) gw[q] += g * sw[q];
-            gb += g * sb;
-        }
-        __syncthreads();                          // feat is rewritten for the next tour
-    }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) atomicAdd(a.gw1 + j * 5 + q, gw[q]);
-    atomicAdd(a.gb1 + j, gb);
-}
 
 // ---------------------------------------------------------------- layer 3, loss
 
@@ -214,12 +131,8 @@ cudaError_t mlp_backward(const MlpLayer1Args &l1, const MlpWeights &wt, const fl
     b.dzt = dzt;
     b.gw1 = gw1;
     b.gb1 = gb1;
-    const size_t smem = (size_t)l1.n * 5 * sizeof(float);
-    e = cudaFuncSetAttribute(mlp_layer1_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = mlp_layer1_bwd_tc(b, l1.sm_count > 0 ? l1.sm_count : 1, st);
     if (e != cudaSuccess) return e;
-    // a few blocks per SM, each over many tours: one gradient update per block
-    const int blocks = 4 * (l1.sm_count > 0 ? l1.sm_count : 152);
-    mlp_layer1_backward_kernel<<<T < blocks ? T : blocks, kMlpH, smem, st>>>(b);
     return cudaGetLastError();
 }
 

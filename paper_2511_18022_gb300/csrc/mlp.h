@@ -42,6 +42,8 @@ struct MlpLayer1Args {
 // Layer 1 forward (features, W1, ReLU, mean pool; writes zt) on the tensor
 // cores: tcgen05 MMAs with the accumulators in tensor memory (mlp_tc.cu).
 cudaError_t mlp_layer1_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st);
+// Layer 1 backward (dW1, db1 from dzt) on the tensor cores (mlp_tc.cu).
+cudaError_t mlp_layer1_bwd_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st);
 // Layer 2 forward, U = relu(zt W2^T + b2), on the tensor cores (mlp_tc.cu).
 cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const __nv_bfloat16 *b2, float *U,
                           unsigned int *err, cudaStream_t st);

@@ -342,6 +342,7 @@ constexpr size_t kGSmem = 2 * kGA + 2 * kGB;   // A hi, A lo, B hi, B lo
 // Requested dynamic shared memory: the operands plus padding so that at
 // most two CTAs share an SM (each holds 256 TMEM columns).
 constexpr size_t kGSmemReq = 100 * 1024;
+static_assert(kGSmem <= kGSmemReq, "GEMM operands exceed the requested shared memory");
 constexpr uint32_t kGTmemCols = 256;
 
 struct TcGemm {
@@ -494,6 +495,221 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- layer 1 backward
+//
+// dW1 and db1 on the tensor cores. With m_hk = [pre_hk > 0] the ReLU mask of
+// hidden unit h at position k, the gradient of tour t is
+//     dW1'[h][:] += (dz_th / n) * sum_k m_hk F'[k][:]
+// (F' the 16-column feature rows of the forward pass: hi parts, the 1 of
+// the bias, lo parts), so per tour the contraction is Mask (H x n) times F'
+// (n x 16): the mask is exact in BF16 and F' is the forward operand, and
+// the per-unit factor is applied to the FP32 result. Per chunk of 224
+// positions one CTA recomputes the pre-activations as the forward pass does
+// (two 128 x 224 MMAs into TMEM columns [0, 224) and [256, 480)), turns them
+// into the mask in shared memory (K-major, row h, K = positions), and adds
+// Mask x F'^T into two 128 x 16 accumulators at columns 224 and 480
+// (14 MMA steps each) against F' stored transposed (row = feature, K =
+// position). After the tour's last chunk each thread scales its unit's row
+// by dz_th / n and keeps the sums; they reach the gradient once per CTA.
+constexpr int kBwChunk = 224;                  // positions per chunk (7 x 32)
+constexpr int kBwKc = kBwChunk / 8;            // 28 core-matrix columns along positions
+constexpr size_t kBwMaskHalf = (size_t)128 * kBwChunk * 2;   // one half's mask, BF16
+constexpr size_t kBwF2 = (size_t)16 * kBwChunk * 2;          // F' transposed
+constexpr size_t kBwSmem = 2 * kBwMaskHalf + kBwF2;          // dynamic part
+constexpr uint32_t kBwAcc0 = kBwChunk, kBwAcc1 = 256 + kBwChunk;   // TMEM columns of the two sums
+
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_layer1_bwd_tc_kernel(MlpLayer1Args a)
+{
+    __shared__ __align__(128) unsigned char s_w1[kMlpH * kTcK * 2];      // W1' (H x 16), as forward
+    __shared__ __align__(128) unsigned char s_f[kBwChunk * kTcK * 2];    // F' (224 x 16), as forward
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_part[kTcThreads / 32];
+    __shared__ float s_carry;
+    __shared__ int s_abort;
+    extern __shared__ __align__(128) unsigned char s_dyn[];   // mask half 0 | mask half 1 | F' transposed
+    unsigned char *s_mask = s_dyn, *s_f2 = s_dyn + 2 * kBwMaskHalf;
+
+    const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+    const int n = a.n;
+    const uint32_t w1_s = (uint32_t)__cvta_generic_to_shared(s_w1);
+    const uint32_t f_s = (uint32_t)__cvta_generic_to_shared(s_f);
+    const uint32_t m_s = (uint32_t)__cvta_generic_to_shared(s_mask);
+    const uint32_t f2_s = (uint32_t)__cvta_generic_to_shared(s_f2);
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+
+    for (int e = j; e < kMlpH * kTcK; e += kTcThreads) {
+        const int h = e / kTcK, k = e % kTcK;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+        if (k < kMlpIn1) v = a.w1[h * kMlpIn1 + k];
+        else if (k == kMlpIn1) v = a.b1[h];
+        else if (k < 2 * kMlpIn1 + 1) v = a.w1[h * kMlpIn1 + k - kMlpIn1 - 1];
+        *reinterpret_cast<__nv_bfloat16 *>(s_w1 + tc::kmajor_offset(h, k, 2)) = v;
+    }
+    if (j == 0) {
+        tc::mbar_init(mbar);
+        s_abort = 0;
+    }
+    if (w == 0) tc::tmem_alloc((uint32_t)__cvta_generic_to_shared(&s_tmem), kTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint64_t a_desc0 = tc::smem_desc(w1_s, 128, 256);
+    const uint64_t a_desc1 = tc::smem_desc(w1_s + 16 * 256, 128, 256);
+    const uint64_t b_desc = tc::smem_desc(f_s, 128, 256);
+    const int half = w >> 2;
+    const int hl = 32 * (w & 3) + lane;                  // row within the half
+    const int h = half * 128 + hl;
+    const uint32_t t_row = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+    const uint32_t pre_col = (uint32_t)(half * 256), acc_col = half ? kBwAcc1 : kBwAcc0;
+    unsigned char *my_mask = s_mask + (size_t)half * kBwMaskHalf;
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    const uint32_t one2 = (uint32_t)__bfloat16_as_ushort(one);
+    uint32_t parity = 0;
+    float gw[kMlpIn1 + 1] = {0, 0, 0, 0, 0, 0};
+
+    for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
+        const int32_t *tour = a.tours + (long long)t * n;
+        if (j == 0) s_carry = 0.0f;
+        __syncthreads();
+        int chunk = 0;
+        for (int k0 = 0; k0 < n; k0 += kBwChunk, ++chunk) {
+            // features of positions k0 .. k0 + 223 (thread j < 224: position k0 + j)
+            const int k = k0 + j;
+            const bool valid = j < kBwChunk && k < n;
+            float m = 0.0f;
+            int c = 1;
+            if (valid) {
+                c = min(max(tour[k], 1), n);
+                m = a.cust[(c - 1) * 4 + 2];
+            }
+            float v = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (lane == 31) s_part[w] = v;
+            __syncthreads();
+            float off = s_carry;
+            for (int q = 0; q < w; ++q) off += s_part[q];
+            const float cum = off + v;
+            __nv_bfloat16 f[kTcK];
+#pragma unroll
+            for (int q = 0; q < kTcK; ++q) f[q] = zero;
+            if (valid) {
+                const float v5[kMlpIn1] = {a.cust[(c - 1) * 4 + 0], a.cust[(c - 1) * 4 + 1], m,
+                                           a.cust[(c - 1) * 4 + 3], cum - floorf(cum)};
+#pragma unroll
+                for (int q = 0; q < kMlpIn1; ++q) {
+                    f[q] = __float2bfloat16_rn(v5[q]);
+                    f[q + kMlpIn1 + 1] = __float2bfloat16_rn(v5[q] - __bfloat162float(f[q]));
+                }
+                f[kMlpIn1] = one;
+            }
+            if (j < kBwChunk) {
+#pragma unroll
+                for (int half_k = 0; half_k < 2; ++half_k) {
+                    uint32_t pw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        pw[q] = (uint32_t)__bfloat16_as_ushort(f[half_k * 8 + 2 * q]) |
+                                ((uint32_t)__bfloat16_as_ushort(f[half_k * 8 + 2 * q + 1]) << 16);
+                    *reinterpret_cast<uint4 *>(s_f + tc::kmajor_offset(j, half_k * 8, 2)) =
+                        make_uint4(pw[0], pw[1], pw[2], pw[3]);
+                }
+                // the same values transposed: row = feature, K = position
+#pragma unroll
+                for (int q = 0; q < kTcK; ++q)
+                    *reinterpret_cast<__nv_bfloat16 *>(s_f2 + tc::kmajor_offset(q, j, kBwKc)) = f[q];
+            }
+            // the scan carry: the last position of this chunk (thread 223)
+            __syncthreads();
+            if (j == kBwChunk - 1) s_carry = cum;
+            tc::fence_operands();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            const int cnt = min(kBwChunk, n - k0);
+            const uint32_t ncols = (uint32_t)((cnt + 31) / 32 * 32);
+            if (j == 0) {
+                const uint32_t idesc = tc::instr_desc(ncols);
+                tc::mma_bf16(tmem, a_desc0, b_desc, idesc, false);
+                tc::mma_bf16(tmem + 256, a_desc1, b_desc, idesc, false);
+                tc::mma_commit(mbar);
+            }
+            if (!tc::mbar_wait(mbar, parity)) {
+                atomicOr(a.err, 1u);
+                s_abort = 1;
+            }
+            parity ^= 1u;
+            tc::fence_after_sync();
+            __syncthreads();
+            if (s_abort) break;
+            // the mask of this thread's unit: 8 positions per 16-byte store
+            for (uint32_t col = 0; col < (uint32_t)kBwChunk; col += 32) {
+                float r[32];
+                if (col < ncols) tc::tmem_ld32(t_row + pre_col + col, r);
+#pragma unroll
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    uint32_t pw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool m0 = col < ncols && r[g8 * 8 + 2 * q] > 0.0f;
+                        const bool m1 = col < ncols && r[g8 * 8 + 2 * q + 1] > 0.0f;
+                        pw[q] = (m0 ? one2 : 0u) | ((m1 ? one2 : 0u) << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(my_mask + tc::kmajor_offset(hl, (int)col + 8 * g8, kBwKc)) =
+                        make_uint4(pw[0], pw[1], pw[2], pw[3]);
+                }
+            }
+            tc::fence_operands();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (j == 0) {
+                const uint32_t idesc = tc::instr_desc(16);
+                const uint32_t sbo = kBwKc * 128;
+                for (int step = 0; step < kBwChunk / 16; ++step) {
+                    const uint32_t koff = (uint32_t)step * 256;
+                    const uint64_t bd = tc::smem_desc(f2_s + koff, 128, sbo);
+                    tc::mma_bf16(tmem + kBwAcc0, tc::smem_desc(m_s + koff, 128, sbo), bd, idesc,
+                                 chunk > 0 || step > 0);
+                    tc::mma_bf16(tmem + kBwAcc1, tc::smem_desc(m_s + (uint32_t)kBwMaskHalf + koff, 128, sbo), bd,
+                                 idesc, chunk > 0 || step > 0);
+                }
+                tc::mma_commit(mbar);
+            }
+            if (!tc::mbar_wait(mbar, parity)) {
+                atomicOr(a.err, 1u);
+                s_abort = 1;
+            }
+            parity ^= 1u;
+            tc::fence_after_sync();
+            __syncthreads();
+            if (s_abort) break;
+        }
+        if (s_abort) break;
+        // this unit's row of Mask x F'^T: hi columns 0-4, bias 5, lo columns 6-10
+        float r[32];
+        tc::tmem_ld32(t_row + acc_col, r);
+        const float g = a.dzt[(long long)t * kMlpIn2 + h] / (float)n;
+#pragma unroll
+        for (int q = 0; q < kMlpIn1; ++q) gw[q] += g * (r[q] + r[q + kMlpIn1 + 1]);
+        gw[kMlpIn1] += g * r[kMlpIn1];
+        tc::fence_before_sync();
+        __syncthreads();                          // TMEM and shared operands are reused by the next tour
+        tc::fence_after_sync();
+    }
+#pragma unroll
+    for (int q = 0; q < kMlpIn1; ++q) atomicAdd(a.gw1 + h * kMlpIn1 + q, gw[q]);
+    atomicAdd(a.gb1 + h, gw[kMlpIn1]);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
 }  // namespace
 
 cudaError_t mlp_layer2_tc(const float *zt, int T, const __nv_bfloat16 *w2, const __nv_bfloat16 *b2, float *U,
@@ -554,6 +770,16 @@ cudaError_t mlp_grad_w2_tc(const float *dU, const float *zt, int T, float *gw2, 
     g.ldo = kMlpIn2;
     g.err = err;
     return tc_gemm<true, true, false, true>(g, st);
+}
+
+cudaError_t mlp_layer1_bwd_tc(const MlpLayer1Args &l1, int sm_count, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(mlp_layer1_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBwSmem);
+    if (e != cudaSuccess) return e;
+    const int grid = l1.T < sm_count ? l1.T : sm_count;
+    mlp_layer1_bwd_tc_kernel<<<grid, kTcThreads, kBwSmem, st>>>(l1);
+    return cudaGetLastError();
 }
 
 }  // namespace cvrpsd
