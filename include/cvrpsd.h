@@ -86,7 +86,8 @@ typedef struct cvrpsd_ctx cvrpsd_ctx;
 #define CVRPSD_WALK_PARAM_TABLE   2   /* tour table in the launch's parameters: n <= 4032, spt 1,
                                          int16 demands need Q < 32768; rings of 8 or 16 */
 
-/* Launch shape of the Split. threads in {64,128,256} per block, spt
+/* Launch shape of the Split. threads in {64,128,256} per block (512 for the
+ * batched path; single-tour calls then run 256), spt
  * (scenarios per thread) in {1,2}, ring (deque capacity per scenario) in
  * {8,16,32,64} (8 only with the parameter-table walk), variant one of
  * CVRPSD_WALK_*, rounds >= 0: with rounds = 0 every thread walks one
@@ -335,7 +336,8 @@ int cvrpsd_batch_destroy(cvrpsd_batch *batch);
  * Autotuner of the batched path: for every launch shape of the persistent
  * batch kernel -- scenarios per block 32 to 512 (threads {32, 64, 128, 256}
  * x scenarios per thread {1, 2}) x deque ring (window tile) {16, 32, 64},
- * 20 shapes (rings of 64 up to 128 threads) -- create this batch, time its
+ * rings of 64 up to 128 threads, plus 512 threads with rings of 16: 21
+ * shapes -- create this batch, time its
  * graph with CUDA events on `stream` (best of three runs after one warm-up),
  * and check that every tour's sum and infeasible count equal those of the
  * first shape (CVRPSD_ERR_DEVICE_STATUS otherwise). The fastest shape becomes

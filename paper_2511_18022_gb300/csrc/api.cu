@@ -144,7 +144,7 @@ int build_tour_table(cvrpsd_ctx *ctx, const int32_t *tour, int n, const int32_t 
 
 bool valid_shape(int threads, int spt, int ring)
 {
-    return (threads == 64 || threads == 128 || threads == 256) && (spt == 1 || spt == 2) &&
+    return (threads == 64 || threads == 128 || threads == 256 || threads == 512) && (spt == 1 || spt == 2) &&
            (ring == 8 || ring == 16 || ring == 32 || ring == 64);
 }
 
@@ -451,6 +451,7 @@ int split_eval_impl(cvrpsd_ctx *ctx, const int32_t *tour, int32_t n, const int32
         } else {
             DequeShape shape{128, 1, 16};
             if (ctx->cfg.threads) shape = DequeShape{ctx->cfg.threads, ctx->cfg.spt, ctx->cfg.ring};
+            if (shape.threads > 256) shape.threads = 256;   // 512 threads: batched path only
             // The parameter-table walk wherever it applies (one scenario per
             // thread, no predecessor output, n <= 4032, ...).
             // Host buffers keep the global-table walk: its prefetch runs twice
@@ -1089,7 +1090,7 @@ int cvrpsd_batch_autotune(cvrpsd_ctx *ctx, int32_t T, const cvrpsd_tour_desc *to
     bool have_ref = false;
     // Scenarios per block 32..512 (threads x scenarios per thread) x deque
     // ring 16 / 32 / 64 (the window tile), every shape the kernel is compiled for.
-    for (int threads : {32, 64, 128, 256})
+    for (int threads : {32, 64, 128, 256, 512})
         for (int spt : {1, 2})
             for (int ring : {16, 32, 64}) {
                 if (rc < 0 || !batch_shape_compiled(DequeShape{threads, spt, ring})) continue;

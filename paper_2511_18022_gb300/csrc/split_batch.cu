@@ -80,14 +80,14 @@ static cudaError_t launch_one(const BatchParams &b, const DequeShape &shape, int
 }
 
 // Launch shapes compiled for the batch kernel (threads, scenarios per
-// thread, ring): scenarios per block 32..256 (and 512) with rings of 16, 32
-// and 64 entries (64 only up to 128 threads: larger blocks of 64-entry rings
-// leave room for one block per SM).
+// thread, ring): scenarios per block 32..512 with rings of 16, 32 and 64
+// entries (64 only up to 128 threads: larger blocks of 64-entry rings leave
+// room for one block per SM; 512 threads only with rings of 16).
 #define CVRPSD_BATCH_SHAPES(X)                                                                  \
     X(32, 1, 16) X(32, 1, 32) X(32, 1, 64) X(32, 2, 16) X(32, 2, 32) X(32, 2, 64)               \
     X(64, 1, 16) X(64, 1, 32) X(64, 1, 64) X(64, 2, 16) X(64, 2, 32) X(64, 2, 64)               \
     X(128, 1, 16) X(128, 1, 32) X(128, 1, 64) X(128, 2, 16) X(128, 2, 32)                      \
-    X(256, 1, 16) X(256, 1, 32) X(256, 2, 16)
+    X(256, 1, 16) X(256, 1, 32) X(256, 2, 16) X(512, 1, 16)
 
 template <typename DT, bool LCAP>
 static cudaError_t dispatch(const BatchParams &b, const DequeShape &s, int grid, bool configure_only,

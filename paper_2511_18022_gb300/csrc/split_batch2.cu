@@ -149,7 +149,7 @@ static cudaError_t launch2_one(const BatchParams &b, const DequeShape &shape, in
 // Shapes of the batch kernel's list with one scenario per thread.
 #define CVRPSD_BATCH2_SHAPES(X)                                                                 \
     X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64) X(128, 16) X(128, 32)            \
-    X(128, 64) X(256, 16) X(256, 32)
+    X(128, 64) X(256, 16) X(256, 32) X(512, 16)
 
 template <bool LCAP>
 static cudaError_t dispatch2(const BatchParams &b, const DequeShape &s, int grid, bool configure_only,

@@ -450,3 +450,15 @@ def test_overflow_then_back_pops_stay_bounded(sp, cv):
         # the ray's deque peaks near 31 entries: it overflows rings of 8 or 16 only
         assert sp.stats()["variant"] == v
         assert (sp.stats()["overflow"] > 0) == (shape[2] <= 16)
+
+
+def test_512_threads_is_batch_only(sp, cv):
+    """threads = 512 is a batched-path shape: a single-tour call configured
+    with it runs 256 threads (the nearest shape that applies) and still
+    matches the oracle."""
+    w = workload("corr-n200", S=1500)
+    inst = w.instances[0]
+    D = demand_matrix(inst.mu, inst.region, w.kind, w.scen_seeds[0], 1500, dtype=np.int16)
+    sp.configure(kernel=cv.KERNEL_DEQUE, threads=512, spt=1, ring=16)
+    check_parity(sp, inst, D)
+    assert sp.stats()["threads"] == 256
