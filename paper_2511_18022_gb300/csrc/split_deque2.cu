@@ -6,13 +6,13 @@
 namespace cvrpsd {
 
 cudaError_t dispatch_deque2_i16_cap_fast(const Walk2Params &p, const void *tab, const DequeShape &s, long long grid,
-                                         int *occ, cudaStream_t st);
+                                         cudaStream_t st);
 cudaError_t dispatch_deque2_i16_nocap_fast(const Walk2Params &p, const void *tab, const DequeShape &s,
-                                           long long grid, int *occ, cudaStream_t st);
+                                           long long grid, cudaStream_t st);
 cudaError_t dispatch_deque2_general(const Walk2Params &p, const void *tab, int esize, bool lcap, bool nowrap,
-                                    bool large, const DequeShape &s, long long grid, int *occ, cudaStream_t st);
+                                    bool large, const DequeShape &s, long long grid, cudaStream_t st);
 cudaError_t dispatch_deque2_i32(const Walk2Params &p, const void *tab, bool lcap, bool nowrap, bool large,
-                                const DequeShape &s, long long grid, int *occ, cudaStream_t st);
+                                const DequeShape &s, long long grid, cudaStream_t st);
 
 // A launch's parameters may take at most 32764 bytes.
 static_assert(sizeof(TabParam<kTab2Large>) + sizeof(Walk2Params) <= 32764, "tour table too large for the parameters");
@@ -25,25 +25,15 @@ static cudaError_t launch2(const Walk2Params &p, const void *tab, long long grid
     return cudaGetLastError();
 }
 
-template <typename DT, int R, int T, bool LCAP, bool NOWRAP, int CAP>
-static cudaError_t occupancy2(int *blocks)
-{
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, split_deque2_kernel<DT, R, T, LCAP, NOWRAP, CAP>, T,
-                                                         0);
-}
-
 // One instantiation class: demand type, route-length cap, key range, table
 // capacity. `shapes` lists the (threads, ring) pairs compiled for it; others
 // fall back to (128, 16).
 #define CVRPSD_D2_SHAPE(T_, R_)                                                                        \
-    if (s.threads == T_ && s.ring == R_) {                                                            \
-        if (occ) return occupancy2<DT, R_, T_, LCAP, NOWRAP, CAP>(occ);                               \
-        return launch2<DT, R_, T_, LCAP, NOWRAP, CAP>(p, tab, grid, st);                              \
-    }
+    if (s.threads == T_ && s.ring == R_) return launch2<DT, R_, T_, LCAP, NOWRAP, CAP>(p, tab, grid, st);
 
 template <typename DT, bool LCAP, bool NOWRAP, int CAP>
 static cudaError_t dispatch_wide(const Walk2Params &p, const void *tab, const DequeShape &s, long long grid,
-                                 int *occ, cudaStream_t st)
+                                 cudaStream_t st)
 {
     CVRPSD_D2_SHAPE(64, 8) CVRPSD_D2_SHAPE(64, 16) CVRPSD_D2_SHAPE(128, 8) CVRPSD_D2_SHAPE(128, 16)
     CVRPSD_D2_SHAPE(256, 8) CVRPSD_D2_SHAPE(256, 16)
@@ -52,7 +42,7 @@ static cudaError_t dispatch_wide(const Walk2Params &p, const void *tab, const De
 
 template <typename DT, bool LCAP, bool NOWRAP, int CAP>
 static cudaError_t dispatch_narrow(const Walk2Params &p, const void *tab, const DequeShape &s, long long grid,
-                                   int *occ, cudaStream_t st)
+                                   cudaStream_t st)
 {
     CVRPSD_D2_SHAPE(128, 16)
     return cudaErrorInvalidValue;
@@ -61,8 +51,8 @@ static cudaError_t dispatch_narrow(const Walk2Params &p, const void *tab, const 
 
 #if CVRPSD_DEQUE2_PART == 0
 cudaError_t dispatch_deque2_i16_cap_fast(const Walk2Params &p, const void *tab, const DequeShape &s, long long grid,
-                                         int *occ, cudaStream_t st)
-{ return dispatch_wide<int16_t, true, true, kTab2Small>(p, tab, s, grid, occ, st); }
+                                         cudaStream_t st)
+{ return dispatch_wide<int16_t, true, true, kTab2Small>(p, tab, s, grid, st); }
 
 namespace {
 
@@ -76,19 +66,18 @@ bool keys_fit(const SplitParams &p, int esize)
     return K * (n * Q + last + Q) + n < (1LL << 31);
 }
 
-// Picks the compiled kernel class of this Split and calls it (occ != nullptr:
-// report occupancy instead of launching).
+// Picks the compiled kernel class of this Split and launches it.
 cudaError_t route(const Walk2Params &w, const void *tab, const SplitParams &p, int esize, const DequeShape &s,
-                  long long grid, int *occ, cudaStream_t st)
+                  long long grid, cudaStream_t st)
 {
     const bool lcap = p.L < p.n, nowrap = keys_fit(p, esize), large = p.n > kTab2Small;
-    if (esize == 4) return dispatch_deque2_i32(w, tab, lcap, nowrap, large, s, grid, occ, st);
+    if (esize == 4) return dispatch_deque2_i32(w, tab, lcap, nowrap, large, s, grid, st);
     if (nowrap && !large) {
-        cudaError_t e = lcap ? dispatch_deque2_i16_cap_fast(w, tab, s, grid, occ, st)
-                             : dispatch_deque2_i16_nocap_fast(w, tab, s, grid, occ, st);
+        cudaError_t e = lcap ? dispatch_deque2_i16_cap_fast(w, tab, s, grid, st)
+                             : dispatch_deque2_i16_nocap_fast(w, tab, s, grid, st);
         if (e != cudaErrorInvalidValue) return e;
     }
-    return dispatch_deque2_general(w, tab, esize, lcap, nowrap, large, s, grid, occ, st);
+    return dispatch_deque2_general(w, tab, esize, lcap, nowrap, large, s, grid, st);
 }
 
 // The shape that runs: the requested one if its class compiles it, else (128, 16).
@@ -154,20 +143,20 @@ cudaError_t launch_split_deque2(const SplitParams &p, const TourStep *tab, int e
     const long long tiles = (p.S + s.threads - 1) / s.threads;
     const long long grid = rounds > 0 ? (tiles + rounds - 1) / rounds : tiles;
     w.stride = grid * s.threads;
-    return route(w, large ? (const void *)&big : (const void *)&small, p, esize, s, grid, nullptr, stream);
+    return route(w, large ? (const void *)&big : (const void *)&small, p, esize, s, grid, stream);
 }
 #elif CVRPSD_DEQUE2_PART == 1
 cudaError_t dispatch_deque2_i16_nocap_fast(const Walk2Params &p, const void *tab, const DequeShape &s,
-                                           long long grid, int *occ, cudaStream_t st)
-{ return dispatch_wide<int16_t, false, true, kTab2Small>(p, tab, s, grid, occ, st); }
+                                           long long grid, cudaStream_t st)
+{ return dispatch_wide<int16_t, false, true, kTab2Small>(p, tab, s, grid, st); }
 #elif CVRPSD_DEQUE2_PART == 2
 // Every other combination, with the (128, 16) shape only.
 cudaError_t dispatch_deque2_general(const Walk2Params &p, const void *tab, int esize, bool lcap, bool nowrap,
-                                    bool large, const DequeShape &s, long long grid, int *occ, cudaStream_t st)
+                                    bool large, const DequeShape &s, long long grid, cudaStream_t st)
 {
 #define CVRPSD_D2_CLASS(DT_, LCAP_, NOWRAP_, CAP_)                                                     \
     if ((esize == (int)sizeof(DT_)) && lcap == LCAP_ && nowrap == NOWRAP_ && (CAP_ == kTab2Large) == large) \
-        return dispatch_narrow<DT_, LCAP_, NOWRAP_, CAP_>(p, tab, s, grid, occ, st);
+        return dispatch_narrow<DT_, LCAP_, NOWRAP_, CAP_>(p, tab, s, grid, st);
     CVRPSD_D2_CLASS(int16_t, true, false, kTab2Small) CVRPSD_D2_CLASS(int16_t, false, false, kTab2Small)
     CVRPSD_D2_CLASS(int16_t, true, true, kTab2Large) CVRPSD_D2_CLASS(int16_t, false, true, kTab2Large)
     CVRPSD_D2_CLASS(int16_t, true, false, kTab2Large) CVRPSD_D2_CLASS(int16_t, false, false, kTab2Large)
@@ -176,11 +165,11 @@ cudaError_t dispatch_deque2_general(const Walk2Params &p, const void *tab, int e
 }
 #elif CVRPSD_DEQUE2_PART == 3
 cudaError_t dispatch_deque2_i32(const Walk2Params &p, const void *tab, bool lcap, bool nowrap, bool large,
-                                const DequeShape &s, long long grid, int *occ, cudaStream_t st)
+                                const DequeShape &s, long long grid, cudaStream_t st)
 {
 #define CVRPSD_D2_CLASS(LCAP_, NOWRAP_, CAP_)                                                          \
     if (lcap == LCAP_ && nowrap == NOWRAP_ && (CAP_ == kTab2Large) == large)                          \
-        return dispatch_narrow<int32_t, LCAP_, NOWRAP_, CAP_>(p, tab, s, grid, occ, st);
+        return dispatch_narrow<int32_t, LCAP_, NOWRAP_, CAP_>(p, tab, s, grid, st);
     CVRPSD_D2_CLASS(true, true, kTab2Small) CVRPSD_D2_CLASS(false, true, kTab2Small)
     CVRPSD_D2_CLASS(true, false, kTab2Small) CVRPSD_D2_CLASS(false, false, kTab2Small)
     CVRPSD_D2_CLASS(true, true, kTab2Large) CVRPSD_D2_CLASS(false, true, kTab2Large)
