@@ -393,6 +393,18 @@ int cvrpsd_topk(cvrpsd_ctx *ctx, const float *d_scores, int32_t M, int32_t k, in
 int cvrpsd_gather_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t rows, int32_t n,
                         const int32_t *d_idx, int32_t R, int32_t *d_out, void *stream);
 
+/* The search's improvement step (the fixed-budget search of Section 4.3):
+ * among T candidate tours d_tours [T][n] with exact costs d_cost [T] (e.g.
+ * the d_mean of cvrpsd_split_eval_tours), take the cheapest, the smallest
+ * index among equal costs (a NaN cost is never taken), and accept it if it
+ * is strictly cheaper than *d_cur_cost: then it is copied to d_cur [n] and
+ * its cost stored in *d_cur_cost. d_trace (optional, one double) receives
+ * *d_cur_cost after the step. d_cur must not overlap d_tours
+ * (CVRPSD_ERR_ARG). One kernel on `stream`; nothing waits. */
+int cvrpsd_accept_best(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, int32_t n,
+                       const double *d_cost, int32_t *d_cur, double *d_cur_cost, double *d_trace,
+                       void *stream);
+
 /* Surrogate of a tour's SAA cost for screening neighbours (not part of the
  * paper's method). Per position k it sees (x, y, mean demand, demand sd,
  * fractional part of the cumulative mean demand / Q) of the customer there;

@@ -23,7 +23,7 @@ __all__ = [
     "cvrpsd_last_stats", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc", "cvrpsd_check_inputs", "cvrpsd_int_rate", "cvrpsd_set_log", "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_split_eval_noalloc",
     "cvrpsd_batch_create", "cvrpsd_batch_autotune", "cvrpsd_batch_run", "cvrpsd_batch_results", "cvrpsd_batch_destroy",
     "cvrpsd_split_eval_batch", "Batch", "cvrpsd_autotune", "cvrpsd_split_routes", "routes_from_pred",
-    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
+    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "cvrpsd_accept_best", "Surrogate", "cvrpsd_gen_demand", "cvrpsd_version",
     "Splitter", "SplitResult", "CvrpsdError", "I16", "I32", "MAX_N", "KERNEL_AUTO",
     "KERNEL_DEQUE", "KERNEL_WARP", "KERNEL_SEQPAR", "GEN_NORMAL", "GEN_CORRELATED",
     "WALK_AUTO", "WALK_GLOBAL_TABLE", "WALK_PARAM_TABLE",
@@ -382,6 +382,22 @@ def cvrpsd_gather_tours(ctx, tours, idx, out, stream=None):
                                                     int(tours.shape[1]),
                                                     _dptr(idx, torch.int32, "idx"), int(idx.shape[0]),
                                                     _dptr(out, torch.int32, "out"), _stream_ptr(stream)))
+
+
+def cvrpsd_accept_best(ctx, tours, cost, cur, cur_cost, trace=None, stream=None):
+    """The search's improvement step on the device: the cheapest of the tours
+    [T][n] (costs float64 [T]) replaces `cur` [n] if strictly cheaper than
+    `cur_cost` (float64, one element); `trace` (optional float64, one element)
+    gets the current cost after the step. Asynchronous."""
+    import torch
+    T, n = int(tours.shape[0]), int(tours.shape[1])
+    if cost.numel() < T or cur.numel() != n or cur_cost.numel() < 1 or (trace is not None and trace.numel() < 1):
+        raise CvrpsdError(_lib.ERR_ARG, f"cost needs {T} entries, cur {n}, cur_cost and trace one")
+    _lib.check(ctx, _lib.load().cvrpsd_accept_best(ctx, _dptr(tours, torch.int32, "tours"), T, n,
+                                                   _dptr(cost, torch.float64, "cost"), _dptr(cur, torch.int32, "cur"),
+                                                   _dptr(cur_cost, torch.float64, "cur_cost"),
+                                                   None if trace is None else _dptr(trace, torch.float64, "trace"),
+                                                   _stream_ptr(stream)))
 
 
 class Surrogate:

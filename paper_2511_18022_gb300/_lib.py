@@ -34,7 +34,7 @@ EXPORTS = [
     "cvrpsd_split_eval", "cvrpsd_split_eval_host", "cvrpsd_gen_demand", "cvrpsd_set_profiling", "cvrpsd_debug_fail_alloc",
     "cvrpsd_check_inputs", "cvrpsd_set_log", "cvrpsd_split_eval_noalloc", "cvrpsd_batch_create", "cvrpsd_batch_run", "cvrpsd_batch_results",
     "cvrpsd_batch_destroy", "cvrpsd_batch_autotune", "cvrpsd_split_eval_batch", "cvrpsd_autotune", "cvrpsd_split_routes",
-    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours",
+    "cvrpsd_split_eval_tours", "cvrpsd_neighbors", "cvrpsd_topk", "cvrpsd_gather_tours", "cvrpsd_accept_best",
     "cvrpsd_surrogate_create", "cvrpsd_surrogate_destroy", "cvrpsd_surrogate_predict",
     "cvrpsd_surrogate_train_step", "cvrpsd_surrogate_gradients", "cvrpsd_surrogate_params", "cvrpsd_surrogate_state",
     "cvrpsd_surrogate_set_scale", "cvrpsd_int_rate",
@@ -117,6 +117,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.cvrpsd_neighbors.argtypes = [vp, vp, i32, vp, i32, vp, vp]
     lib.cvrpsd_topk.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.cvrpsd_gather_tours.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
+    lib.cvrpsd_accept_best.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
     lib.cvrpsd_surrogate_create.argtypes = [vp, i32, vp, vp, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.cvrpsd_surrogate_destroy.argtypes = [vp]
     lib.cvrpsd_surrogate_predict.argtypes = [vp, vp, i32, vp, vp]

@@ -189,6 +189,8 @@ cudaError_t launch_tour_means(const unsigned long long *acc, int T, long long S,
 cudaError_t launch_topk(const float *scores, int M, int k, int32_t *idx_out, cudaStream_t st);
 cudaError_t launch_gather_rows(const int32_t *in, int rows, int n, const int32_t *idx, int R, int32_t *out,
                                cudaStream_t st);
+cudaError_t launch_accept_best(const int32_t *tours, int T, int n, const double *cost, int32_t *cur,
+                               double *cur_cost, double *trace, cudaStream_t st);
 
 // Copy a [n][ld_in] demand matrix into a [n][ld_out] one of another element
 // type (first S columns); values outside int16 set *saturated (device flag).

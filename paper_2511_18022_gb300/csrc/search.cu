@@ -199,4 +199,55 @@ cudaError_t launch_gather_rows(const int32_t *in, int rows, int n, const int32_t
     return cudaGetLastError();
 }
 
+// The search's acceptance, one block: the cheapest of T costs (smallest
+// index among equal costs; a NaN cost compares false and is never taken),
+// accepted when strictly cheaper than *cur_cost, in which case its tour
+// replaces cur. trace (optional) gets the current cost after the step.
+constexpr int kAcceptThreads = 256;
+
+__global__ void __launch_bounds__(kAcceptThreads) accept_best_kernel(const int32_t *tours, int T, int n,
+                                                                     const double *cost, int32_t *cur,
+                                                                     double *cur_cost, double *trace)
+{
+    __shared__ double s_c[kAcceptThreads / 32];
+    __shared__ int s_i[kAcceptThreads / 32];
+    __shared__ int s_take;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    double best = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    int bi = T;                                                   // none yet
+    for (int j = tid; j < T; j += kAcceptThreads) {
+        const double c = cost[j];
+        if (c < best) best = c, bi = j;       // ascending j: the first of equal costs stays
+    }
+    // (cost, index) minimum over the block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oc = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oc < best || (oc == best && oi < bi)) best = oc, bi = oi;
+    }
+    if (lane == 0) s_c[w] = best, s_i[w] = bi;
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 1; k < kAcceptThreads / 32; ++k)
+            if (s_c[k] < best || (s_c[k] == best && s_i[k] < bi)) best = s_c[k], bi = s_i[k];
+        const double cc = *cur_cost;
+        const bool take = bi < T && best < cc;
+        if (take) *cur_cost = best;
+        if (trace) *trace = take ? best : cc;
+        s_take = take ? bi : -1;
+    }
+    __syncthreads();
+    const int b = s_take;
+    if (b >= 0)
+        for (int k = tid; k < n; k += kAcceptThreads) cur[k] = tours[(long long)b * n + k];
+}
+
+cudaError_t launch_accept_best(const int32_t *tours, int T, int n, const double *cost, int32_t *cur,
+                               double *cur_cost, double *trace, cudaStream_t st)
+{
+    accept_best_kernel<<<1, kAcceptThreads, 0, st>>>(tours, T, n, cost, cur, cur_cost, trace);
+    return cudaGetLastError();
+}
+
 }  // namespace cvrpsd

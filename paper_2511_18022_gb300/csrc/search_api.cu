@@ -220,6 +220,25 @@ int cvrpsd_gather_tours(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t rows, i
     return CVRPSD_OK;
 }
 
+int cvrpsd_accept_best(cvrpsd_ctx *ctx, const int32_t *d_tours, int32_t T, int32_t n, const double *d_cost,
+                       int32_t *d_cur, double *d_cur_cost, double *d_trace, void *stream)
+{
+    CVRPSD_TRACE("cvrpsd_accept_best");
+    if (!ctx) return CVRPSD_ERR_ARG;
+    if (T < 1 || n < 1) return fail(ctx, CVRPSD_ERR_ARG, "T = %d, n = %d", T, n);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!is_device_ptr(d_tours, ctx->device) || !is_device_ptr(d_cost, ctx->device) ||
+        !is_device_ptr(d_cur, ctx->device) || !is_device_ptr(d_cur_cost, ctx->device) ||
+        (d_trace && !is_device_ptr(d_trace, ctx->device)))
+        return fail(ctx, CVRPSD_ERR_ARG, "tours, cost, cur, cur_cost and trace must be device memory");
+    const uintptr_t t0 = (uintptr_t)d_tours, t1 = t0 + (uintptr_t)T * (uintptr_t)n * sizeof(int32_t);
+    const uintptr_t c0 = (uintptr_t)d_cur, c1 = c0 + (uintptr_t)n * sizeof(int32_t);
+    if (c0 < t1 && t0 < c1) return fail(ctx, CVRPSD_ERR_ARG, "cur overlaps the candidate tours");
+    CK(launch_accept_best(d_tours, T, n, d_cost, d_cur, d_cur_cost, d_trace, reinterpret_cast<cudaStream_t>(stream)),
+       "accept");
+    return CVRPSD_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ surrogate

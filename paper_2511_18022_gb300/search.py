@@ -21,7 +21,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (Surrogate, cvrpsd_gather_tours, cvrpsd_neighbors, cvrpsd_split_eval_tours, cvrpsd_topk)
+from . import (Surrogate, cvrpsd_accept_best, cvrpsd_gather_tours, cvrpsd_neighbors, cvrpsd_split_eval_tours,
+               cvrpsd_topk)
 
 
 def random_moves(rng: np.random.Generator, M: int, n: int) -> np.ndarray:
@@ -120,7 +121,9 @@ class LocalSearch:
         self.scale = scale
         self.lr = lr
         self.new_tours, self.new_costs = [], []
-        self._trace = []
+        self._trace = []                  # device chunks of the cost trace
+        self._trace_chunk = 1024
+        self._tpos = self._trace_chunk
         self.log = SearchLog()
 
     @property
@@ -157,12 +160,14 @@ class LocalSearch:
         else:
             chosen = self.cand[: self.k]
         costs = self.eval(chosen)
-        b = torch.argmin(costs).view(1)
-        c = costs.index_select(0, b)
-        better = c < self.cur_cost_t
-        self.cur.copy_(torch.where(better, chosen.index_select(0, b)[0], self.cur))
-        self.cur_cost_t = torch.minimum(self.cur_cost_t, c)
-        self._trace.append(self.cur_cost_t)
+        # the cheapest candidate replaces the current tour if strictly
+        # cheaper; the cost after the step goes to the device trace
+        if self._tpos == self._trace_chunk:
+            self._trace.append(torch.empty(self._trace_chunk, dtype=torch.float64, device=costs.device))
+            self._tpos = 0
+        cvrpsd_accept_best(self.ctx, chosen, costs, self.cur, self.cur_cost_t,
+                           trace=self._trace[-1][self._tpos:self._tpos + 1])
+        self._tpos += 1
         self.log.screened += self.M
         self.log.evaluated += self.k
         if self.sur is not None and self.retrain_every:
@@ -197,8 +202,10 @@ class LocalSearch:
         log.costs (step() alone only appends to the device trace)."""
         import torch
         if self._trace:
-            self.log.costs.extend(torch.cat(self._trace).tolist())
+            last = self._trace[-1][:self._tpos]
+            self.log.costs.extend(torch.cat(self._trace[:-1] + [last]).tolist())
             self._trace = []
+            self._tpos = self._trace_chunk
 
     @property
     def iterations(self) -> int:

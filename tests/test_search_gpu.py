@@ -109,6 +109,46 @@ def test_topk(sp, cv, M, k):
     assert out.cpu().numpy().tolist() == want.tolist()
 
 
+@pytest.mark.parametrize("T,case", [(1, "better"), (7, "tie"), (300, "tie"), (64, "worse"), (33, "nan"),
+                                    (513, "equal")])
+def test_accept_best(sp, cv, T, case):
+    """cvrpsd_accept_best against the rule written out on the host: the
+    cheapest candidate (first of equal costs, NaN never), taken only if
+    strictly below the current cost; the trace holds the cost after."""
+    rng = np.random.default_rng(T)
+    n = 37
+    tours = rng.integers(1, 1000, size=(T, n)).astype(np.int32)
+    cost = rng.uniform(100, 200, T)
+    cur0 = np.arange(1, n + 1, dtype=np.int32)
+    cc0 = 150.0
+    if case == "better":
+        cost[0] = 99.0
+    elif case == "tie":
+        cost[T // 3] = cost[T - 1] = 50.0            # equal minima: the first wins
+    elif case == "worse":
+        cost[:] = rng.uniform(151, 200, T)
+    elif case == "nan":
+        cost[:] = np.nan
+        cost[5] = 120.0
+    elif case == "equal":
+        cost[:] = rng.uniform(150.5, 200, T)
+        cost[200] = cc0                               # not strictly cheaper
+    key = np.where(np.isnan(cost), np.inf, cost)
+    b = int(np.argmin(key))
+    take = key[b] < cc0
+    want_cur = tours[b] if take else cur0
+    want_c = key[b] if take else cc0
+    d_cur = torch.from_numpy(cur0.copy()).cuda()
+    d_cc = torch.tensor([cc0], dtype=torch.float64, device="cuda")
+    trace = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    d_tours = torch.from_numpy(tours).cuda()
+    cv.cvrpsd_accept_best(sp.ctx, d_tours, torch.from_numpy(cost).cuda(), d_cur, d_cc, trace=trace)
+    assert d_cur.cpu().numpy().tolist() == want_cur.tolist()
+    assert d_cc.item() == want_c and trace.item() == want_c
+    with pytest.raises(cv.CvrpsdError):
+        cv.cvrpsd_accept_best(sp.ctx, d_tours, torch.from_numpy(cost).cuda(), d_tours[0], d_cc)
+
+
 def surrogate_case(cv, sp, T=48, n=60, seed=0):
     inst = make_instance(n, 5, 20, seed=seed, Q=64)
     rng = np.random.default_rng(seed)
