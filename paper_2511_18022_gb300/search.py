@@ -77,12 +77,13 @@ class LocalSearch:
 
     An iteration never waits for the device: the moves of the next
     `moves_block` iterations are drawn on the host and copied at once, the
-    best evaluated neighbour is chosen and accepted by device-side tensor
-    operations, and the per-iteration costs are read back when run() ends."""
+    best evaluated neighbour is chosen and accepted on the device
+    (cvrpsd_accept_best), and the per-iteration costs, kept on the device in
+    chunks of `trace_chunk`, are read back when run() ends."""
 
     def __init__(self, ctx, inst, D, start, *, surrogate: Surrogate | None = None, M: int = 4096, k: int = 64,
                  seed: int = 0, retrain_every: int = 0, scale=(0.0, 1.0), lr: float = 2e-4,
-                 moves_block: int = 64, exact_all: bool = False, explore: int = 0):
+                 moves_block: int = 64, exact_all: bool = False, explore: int = 0, trace_chunk: int = 1024):
         """Three modes: with a surrogate, screen M neighbours and split the k
         best exactly; with exact_all, split all M neighbours exactly (the
         plain-Split search the screened one is measured against: same moves
@@ -122,7 +123,7 @@ class LocalSearch:
         self.lr = lr
         self.new_tours, self.new_costs = [], []
         self._trace = []                  # device chunks of the cost trace
-        self._trace_chunk = 1024
+        self._trace_chunk = max(1, int(trace_chunk))
         self._tpos = self._trace_chunk
         self.log = SearchLog()
 

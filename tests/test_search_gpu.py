@@ -310,7 +310,8 @@ def test_local_search_matches_host_accept_rule(sp, cv):
     dD = torch.from_numpy(D).cuda()
     start = np.random.default_rng(2).permutation(np.arange(1, inst.n + 1)).astype(np.int32)
     k, iters = 16, 100
-    ls = search.LocalSearch(sp.ctx, inst, dD, start, k=k, seed=77, moves_block=8)
+    # a trace chunk of 7 costs: the device trace rolls over 14 times
+    ls = search.LocalSearch(sp.ctx, inst, dD, start, k=k, seed=77, moves_block=8, trace_chunk=7)
     for _ in range(iters):
         ls.step()
     ls.flush()
